@@ -1,0 +1,359 @@
+// Tunable FP32 2-D cross-correlation kernels for sm_103a.
+//
+//   out[y][x] = sum_{j<fh} sum_{i<fw} in[y+j][x+i] * filt[j][i]
+//
+// (the workload's "zero-padded input" convolution, computed as a correlation:
+// no filter flip).  Every variant accumulates each output in one FP32 register
+// with an fmaf chain over the taps in the same order -- j ascending, then i
+// ascending -- so all tuning configurations give bitwise-identical results.
+//
+// Tunable parameters (the tuner's search space):
+//   block_x, block_y  threads per CTA in x / y (runtime: blockDim)
+//   TX, TY            outputs per thread in x / y (compile time: register tile)
+//   staging           DIRECT: each thread reads its rows straight from global
+//                     memory (vector loads through L1), the horizontal halo of
+//                     a row comes from neighbouring lanes by warp shuffles;
+//                     SMEM: the CTA's halo tile is copied to shared memory with
+//                     cp.async; TMA: the same tile arrives by one 2-D
+//                     cp.async.bulk.tensor copy completing on an mbarrier
+//   filter memory     CONST: taps are read from the kernel's parameter space
+//                     (constant bank, an immediate FFMA operand once the tap
+//                     loops are unrolled); SHARED: taps are copied to shared
+//                     memory first and read with LDS
+//   vec_width         width (floats) of global loads and stores
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "conv2d_launch.h"
+
+namespace convtune {
+
+// Launch arguments.  The filter travels by value in the parameter space, i.e.
+// in the constant bank.
+template <int NTAPS>
+struct alignas(64) ConvArgs {
+  CUtensorMap tmap;          // TMA descriptor of the padded input (TMA staging)
+  const float* in;           // padded input, in_h rows of in_pitch floats
+  float* out;                // output, out_h rows of out_pitch floats
+  unsigned* status;          // device status word (error bits), may be null
+  long long in_pitch, out_pitch;
+  int in_h, in_w, out_h, out_w;
+  int fh, fw;                // used by the generic kernel only
+  int vw;                    // global load width 1, 2 or 4
+  int staging;               // kStageDirect / kStageSmem / kStageTma
+  int smem_pitch;            // floats per shared-memory tile row
+  int tile_w, tile_h;        // staged tile (floats); tile_w % 4 == 0
+  float w[NTAPS];            // taps, row-major fh x fw
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// ----------------------------------------------------------------------------
+// Global loads of n (= 1, 2, 4) consecutive floats starting at column c of a
+// row.  Columns >= in_w read as zero (they feed only outputs that are never
+// stored); rows outside [0, in_h) read as zero.
+// ----------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void load_run(float (&v)[N], const float* row, int c, int in_w,
+                                         bool row_ok, int vw) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) v[q] = 0.0f;
+  if (!row_ok) return;
+  if (c + N <= in_w) {
+    if constexpr (N == 4) {
+      if (vw >= 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(row + c));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        return;
+      }
+    }
+    if constexpr (N % 2 == 0) {
+      if (vw >= 2) {
+#pragma unroll
+        for (int q = 0; q < N; q += 2) {
+          const float2 t = __ldg(reinterpret_cast<const float2*>(row + c + q));
+          v[q] = t.x; v[q + 1] = t.y;
+        }
+        return;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = __ldg(row + c + q);
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    if (c + q < in_w) v[q] = __ldg(row + c + q);
+}
+
+// ----------------------------------------------------------------------------
+// Halo tile staging: rows [gy0, gy0 + tile_h) x columns [gx0, gx0 + tile_w)
+// of the padded input into shared memory (pitch sp floats).  Outside the input
+// the tile holds zeros.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async_bytes(float* dst, const float* src, int cp_bytes,
+                                               int src_bytes) {
+  const unsigned d = smem_u32(dst);
+  if (cp_bytes == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes));
+  } else if (cp_bytes == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes));
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes));
+  }
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <class Args>
+__device__ __forceinline__ void stage_tile_cp_async(const Args& a, float* tile, int gx0, int gy0) {
+  const int vw = a.vw;
+  const int chunks_per_row = a.tile_w / vw;
+  const int total = chunks_per_row * a.tile_h;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int c = threadIdx.y * blockDim.x + threadIdx.x; c < total; c += nthr) {
+    const int r = c / chunks_per_row;
+    const int col = (c - r * chunks_per_row) * vw;
+    const int gy = gy0 + r, gx = gx0 + col;
+    int avail = 0;
+    if (gy < a.in_h && gx < a.in_w) avail = min(vw, a.in_w - gx);
+    const float* src = avail > 0 ? a.in + (long long)gy * a.in_pitch + gx : a.in;
+    cp_async_bytes(tile + r * a.smem_pitch + col, src, vw * 4, avail * 4);
+  }
+  cp_async_wait_all();
+}
+
+// One 2-D TMA copy of the tile (tile_w <= 256, tile_h <= 256, x % 4 == 0).
+// Returns false in every thread of the CTA if any thread's bounded wait gave
+// up (status bit set).  Ends with a CTA barrier.
+template <class Args>
+__device__ __forceinline__ bool stage_tile_tma(const Args& a, float* tile, uint64_t* mbar,
+                                               int gx0, int gy0) {
+  const unsigned bar = smem_u32(mbar);
+  const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+  if (leader) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (leader) {
+    const unsigned bytes = static_cast<unsigned>(a.tile_w * a.tile_h * 4);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(tile)),
+        "l"(reinterpret_cast<uint64_t>(&a.tmap)), "r"(gx0), "r"(gy0), "r"(bar)
+        : "memory");
+  }
+  unsigned done = 0;
+  for (unsigned it = 0; it < kMbarSpinLimit; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(0u)
+        : "memory");
+    if (done) break;
+  }
+  // every thread takes the same decision, so no thread is left at a barrier
+  if (__syncthreads_or(!done)) {
+    if (leader && a.status) atomicOr(a.status, kStatusTmaTimeout);
+    return false;
+  }
+  return true;
+}
+
+// ----------------------------------------------------------------------------
+// Row fetch for the direct (register) path: the thread's TX + K - 1 input
+// values of one row.  Each lane loads its own TX values; the halo to its right
+// comes from the next lanes of its x-segment by shuffles (the last lanes take
+// it from the first lanes' second load, one segment further right).
+// ----------------------------------------------------------------------------
+template <int K, int TX>
+__device__ __forceinline__ void fetch_row_direct(float (&rowv)[TX + K - 1], const float* row,
+                                                 bool row_ok, int x0, int xs_next, int lane,
+                                                 int seg, unsigned mask, int in_w, int vw) {
+  float A[TX];
+  load_run<TX>(A, row, x0, in_w, row_ok, vw);
+  constexpr int NB = (TX + K - 2) / TX;  // lanes whose second load is used
+  float B[TX];
+#pragma unroll
+  for (int q = 0; q < TX; ++q) B[q] = 0.0f;
+  if (K > 1 && lane < NB) load_run<TX>(B, row, xs_next + lane * TX, in_w, row_ok, vw);
+#pragma unroll
+  for (int q = 0; q < TX; ++q) rowv[q] = A[q];
+#pragma unroll
+  for (int m = TX; m < TX + K - 1; ++m) {
+    const int d = m / TX, q = m % TX;
+    const float send = lane < d ? B[q] : A[q];
+    rowv[m] = __shfl_sync(mask, send, (lane + d) & (seg - 1), seg);
+  }
+}
+
+// Row fetch from the staged shared-memory tile with the widest aligned LDS.
+template <int K, int TX>
+__device__ __forceinline__ void fetch_row_smem(float (&rowv)[TX + K - 1], const float* srow) {
+  constexpr int N = TX + K - 1;
+  if constexpr (TX % 4 == 0) {
+#pragma unroll
+    for (int m = 0; m < N; m += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(srow + m);
+      rowv[m] = t.x;
+      if (m + 1 < N) rowv[m + 1] = t.y;
+      if (m + 2 < N) rowv[m + 2] = t.z;
+      if (m + 3 < N) rowv[m + 3] = t.w;
+    }
+  } else if constexpr (TX % 2 == 0) {
+#pragma unroll
+    for (int m = 0; m < N; m += 2) {
+      const float2 t = *reinterpret_cast<const float2*>(srow + m);
+      rowv[m] = t.x;
+      if (m + 1 < N) rowv[m + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) rowv[m] = srow[m];
+  }
+}
+
+// Store one thread row of TX outputs (vector width min(vw, TX) when the run
+// is fully inside the output, else element by element).
+template <int TX>
+__device__ __forceinline__ void store_run(float* orow, int x0, int out_w, int vw,
+                                          const float (&v)[TX]) {
+  if (x0 + TX <= out_w) {
+    if constexpr (TX == 4) {
+      if (vw >= 4) {
+        *reinterpret_cast<float4*>(orow + x0) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+      }
+    }
+    if constexpr (TX % 2 == 0) {
+      if (vw >= 2) {
+#pragma unroll
+        for (int q = 0; q < TX; q += 2)
+          *reinterpret_cast<float2*>(orow + x0 + q) = make_float2(v[q], v[q + 1]);
+        return;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < TX; ++q)
+    if (x0 + q < out_w) orow[x0 + q] = v[q];
+}
+
+// ----------------------------------------------------------------------------
+// The tap accumulation of one thread: TY x TX outputs whose top-left output is
+// (y0, x0).  Input rows r = 0 .. TY+K-2 (relative to y0) are fetched once
+// each; row r feeds output row t with filter row j = r - t.  For a fixed
+// output the taps therefore arrive in (j, i) lexicographic order.
+// FROW(r, rowv) fills rowv with the row's TX+K-1 values; TAP(j, i) returns the
+// tap.
+// ----------------------------------------------------------------------------
+template <int K, int TX, int TY, class FetchRow, class Tap>
+__device__ __forceinline__ void accumulate_tile(float (&acc)[TY][TX], FetchRow&& frow, Tap&& tap) {
+#pragma unroll
+  for (int t = 0; t < TY; ++t)
+#pragma unroll
+    for (int x = 0; x < TX; ++x) acc[t][x] = 0.0f;
+#pragma unroll
+  for (int r = 0; r < TY + K - 1; ++r) {
+    float rowv[TX + K - 1];
+    frow(r, rowv);
+#pragma unroll
+    for (int t = 0; t < TY; ++t) {
+      const int j = r - t;
+      if (j >= 0 && j < K) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const float w = tap(j, i);
+#pragma unroll
+          for (int x = 0; x < TX; ++x) acc[t][x] = fmaf(rowv[x + i], w, acc[t][x]);
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Specialised kernel: square odd filter K x K.
+//   STAGED    = false: DIRECT staging; true: SMEM or TMA (args.staging)
+//   FILT_SMEM = false: taps from the parameter (constant) space
+// Dynamic shared memory: [filter K*K (if FILT_SMEM), padded to 32 floats]
+//                        [tile tile_h x smem_pitch (if STAGED)] [mbarrier]
+// ----------------------------------------------------------------------------
+template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM>
+__global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int kFiltFloats = FILT_SMEM ? ((K * K + 31) / 32) * 32 : 0;
+  float* sfilt = reinterpret_cast<float*>(smem_raw);
+  float* tile = reinterpret_cast<float*>(smem_raw) + kFiltFloats;
+
+  const int bx = blockDim.x, by = blockDim.y;
+  const int gx0 = blockIdx.x * bx * TX;  // tile origin (input == output coords)
+  const int gy0 = blockIdx.y * by * TY;
+  const int x0 = gx0 + threadIdx.x * TX;
+  const int y0 = gy0 + threadIdx.y * TY;
+
+  if constexpr (FILT_SMEM) {
+    for (int k = threadIdx.y * bx + threadIdx.x; k < K * K; k += bx * by) sfilt[k] = a.w[k];
+  }
+  if constexpr (STAGED) {
+    if (a.staging == kStageTma) {
+      uint64_t* mbar = reinterpret_cast<uint64_t*>(tile + a.tile_h * a.smem_pitch);
+      if (!stage_tile_tma(a, tile, mbar, gx0, gy0)) return;
+    } else {
+      stage_tile_cp_async(a, tile, gx0, gy0);
+    }
+  }
+  if constexpr (STAGED || FILT_SMEM) __syncthreads();
+
+  float acc[TY][TX];
+  auto tap = [&](int j, int i) -> float {
+    if constexpr (FILT_SMEM) return sfilt[j * K + i];
+    else return a.w[j * K + i];
+  };
+  if constexpr (STAGED) {
+    const float* sbase = tile + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
+    accumulate_tile<K, TX, TY>(
+        acc, [&](int r, float(&rowv)[TX + K - 1]) {
+          fetch_row_smem<K, TX>(rowv, sbase + r * a.smem_pitch);
+        },
+        tap);
+  } else {
+    const int nthr = bx * by;
+    const unsigned mask = nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u);
+    const int seg = bx < 32 ? bx : 32;  // lanes sharing one contiguous x run
+    const int lane = threadIdx.x & (seg - 1);
+    const int xs = gx0 + (threadIdx.x - lane) * TX;
+    const int xs_next = xs + seg * TX;
+    accumulate_tile<K, TX, TY>(
+        acc, [&](int r, float(&rowv)[TX + K - 1]) {
+          const int gy = y0 + r;
+          const bool ok = gy < a.in_h;
+          const float* row = a.in + (long long)(ok ? gy : 0) * a.in_pitch;
+          fetch_row_direct<K, TX>(rowv, row, ok, x0, xs_next, lane, seg, mask, a.in_w, a.vw);
+        },
+        tap);
+  }
+
+#pragma unroll
+  for (int t = 0; t < TY; ++t) {
+    const int y = y0 + t;
+    if (y < a.out_h) store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[t]);
+  }
+}
+
+}  // namespace convtune

@@ -1,0 +1,437 @@
+// libconvtune runtime: validation and launch of the tuned correlation, the
+// device status word, the host-buffer entry point and device facts.
+#include <cudaTypedefs.h>
+#include <limits.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <utility>
+
+#include "runtime.h"
+
+namespace convtune {
+
+namespace {
+
+struct DeviceState {
+  unsigned* status = nullptr;
+  int smem_optin = 0;
+  std::set<std::pair<const void*, size_t>> smem_attr_set;
+  // buffers of the host-buffer entry point
+  float* din = nullptr;
+  size_t din_bytes = 0;
+  float* dout = nullptr;
+  size_t dout_bytes = 0;
+};
+
+std::mutex g_mu;        // guards g_dev
+std::mutex g_host_mu;   // serialises the host-buffer entry point
+std::map<int, DeviceState> g_dev;
+
+DeviceState* current_state(int* dev_out, int* err) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    *err = cuda_status(e);
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState& st = g_dev[dev];
+  if (st.smem_optin == 0) {
+    int v = 0;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) {
+      *err = cuda_status(e);
+      return nullptr;
+    }
+    st.smem_optin = v;
+  }
+  if (dev_out) *dev_out = dev;
+  *err = CT_OK;
+  return &st;
+}
+
+const void* pick_specialised(int k, int tx, int ty, bool staged, bool fs) {
+  switch (k) {
+    case 1: return pick_k1(tx, ty, staged, fs);
+    case 3: return pick_k3(tx, ty, staged, fs);
+    case 5: return pick_k5(tx, ty, staged, fs);
+    case 7: return pick_k7(tx, ty, staged, fs);
+    case 9: return pick_k9(tx, ty, staged, fs);
+    case 11: return pick_k11(tx, ty, staged, fs);
+    case 13: return pick_k13(tx, ty, staged, fs);
+    case 15: return pick_k15(tx, ty, staged, fs);
+    case 17: return pick_k17(tx, ty, staged, fs);
+    default: return nullptr;
+  }
+}
+
+KernelLauncher launcher_for(int k) {
+  switch (k) {
+    case 1: return launch_k1;
+    case 3: return launch_k3;
+    case 5: return launch_k5;
+    case 7: return launch_k7;
+    case 9: return launch_k9;
+    case 11: return launch_k11;
+    case 13: return launch_k13;
+    case 15: return launch_k15;
+    case 17: return launch_k17;
+    default: return nullptr;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+inline bool one_of_124(int v) { return v == 1 || v == 2 || v == 4; }
+
+}  // namespace
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return CT_OK;
+  if (e == cudaErrorInvalidConfiguration || e == cudaErrorLaunchOutOfResources) {
+    cudaGetLastError();
+    return CT_ECONFIG;
+  }
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return CT_ENOMEM;
+  }
+  cudaGetLastError();
+  return CT_ECUDA;
+}
+
+unsigned* device_status_word(int* err) {
+  DeviceState* st = current_state(nullptr, err);
+  if (!st) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!st->status) {
+    unsigned* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, 256);
+    if (e == cudaSuccess) e = cudaMemset(p, 0, 256);
+    if (e != cudaSuccess) {
+      *err = cuda_status(e);
+      return nullptr;
+    }
+    st->status = p;
+  }
+  return st->status;
+}
+
+double conv_flop(const ct_problem& p) {
+  return 2.0 * p.fh * p.fw * (double)p.out_h * (double)p.out_w;
+}
+
+double conv_bytes(const ct_problem& p) {
+  const double in_elems = (double)(p.out_h + p.fh - 1) * (double)(p.out_w + p.fw - 1);
+  return 4.0 * (in_elems + (double)p.out_h * p.out_w + (double)p.fh * p.fw);
+}
+
+int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::string* why) {
+  auto fail = [&](int code, const char* msg) {
+    if (why) *why = msg;
+    return code;
+  };
+  *plan = ConvPlan{};
+  if (p.out_h < 0 || p.out_w < 0) return fail(CT_EINVAL, "negative output size");
+  if (!p.filt) return fail(CT_EINVAL, "null filter");
+  if (p.fh < 1 || p.fw < 1 || p.fh > 32 || p.fw > 32 || p.fh * p.fw > kGenericMaxTaps)
+    return fail(CT_EINVAL, "filter sides must be 1..32 with fh*fw <= 1024");
+  if (p.out_h == 0 || p.out_w == 0) {
+    plan->empty = true;
+    return CT_OK;
+  }
+  if (!p.in || !p.out) return fail(CT_EINVAL, "null input or output");
+  const long long in_w = (long long)p.out_w + p.fw - 1;
+  const long long in_h = (long long)p.out_h + p.fh - 1;
+  if (in_w > (1LL << 30) || in_h > (1LL << 30)) return fail(CT_EINVAL, "problem too large");
+  if (p.in_pitch < in_w) return fail(CT_EINVAL, "in_pitch < out_w + fw - 1");
+  if (p.out_pitch < p.out_w) return fail(CT_EINVAL, "out_pitch < out_w");
+
+  if (c.block_x < 16 || c.block_x > 1024 || (c.block_x != 16 && c.block_x % 32 != 0))
+    return fail(CT_ECONFIG, "block_x must be 16 or a multiple of 32, <= 1024");
+  if (c.block_y < 1 || c.block_x * c.block_y > 1024)
+    return fail(CT_ECONFIG, "block_x * block_y must be 16..1024");
+  if (!one_of_124(c.tile_x) || !one_of_124(c.tile_y)) return fail(CT_ECONFIG, "tile sides 1, 2, 4");
+  if (c.staging < CT_STAGE_DIRECT || c.staging > CT_STAGE_TMA) return fail(CT_ECONFIG, "staging");
+  if (c.filter_mem != CT_FILTER_SHARED && c.filter_mem != CT_FILTER_CONST)
+    return fail(CT_ECONFIG, "filter_mem");
+  if (!one_of_124(c.vec_width)) return fail(CT_ECONFIG, "vec_width 1, 2, 4");
+
+  ConvLaunch& L = plan->L;
+  L.in = p.in;
+  L.out = p.out;
+  L.in_pitch = p.in_pitch;
+  L.out_pitch = p.out_pitch;
+  L.in_h = (int)in_h;
+  L.in_w = (int)in_w;
+  L.out_h = p.out_h;
+  L.out_w = p.out_w;
+  L.fh = p.fh;
+  L.fw = p.fw;
+  L.taps = p.filt;
+  L.bx = c.block_x;
+  L.by = c.block_y;
+
+  const bool specialised = p.fh == p.fw && (p.fh & 1) && p.fh <= kMaxK;
+  plan->specialised = specialised;
+  plan->block = dim3(c.block_x, c.block_y);
+  if (!specialised) {
+    L.tx = L.ty = 1;
+    L.staging = kStageDirect;
+    L.filt_smem = 1;
+    L.vw = 1;
+    L.smem_bytes = sizeof(float) * p.fh * p.fw;
+    plan->fn = pick_generic();
+    plan->grid = dim3((p.out_w + c.block_x - 1) / c.block_x, (p.out_h + c.block_y - 1) / c.block_y);
+  } else {
+    const int K = p.fh;
+    L.tx = c.tile_x;
+    L.ty = c.tile_y;
+    L.staging = c.staging;
+    L.filt_smem = c.filter_mem == CT_FILTER_SHARED;
+    L.vw = c.vec_width;
+    const bool staged = c.staging != CT_STAGE_DIRECT;
+    plan->fn = pick_specialised(K, c.tile_x, c.tile_y, staged, L.filt_smem != 0);
+    if (!plan->fn) return fail(CT_ECONFIG, "variant not compiled");
+    plan->grid = dim3((p.out_w + c.block_x * c.tile_x - 1) / (c.block_x * c.tile_x),
+                      (p.out_h + c.block_y * c.tile_y - 1) / (c.block_y * c.tile_y));
+    const int lw = staged ? c.vec_width : (c.vec_width < c.tile_x ? c.vec_width : c.tile_x);
+    const int sw = c.vec_width < c.tile_x ? c.vec_width : c.tile_x;
+    if (lw > 1 && ((uintptr_t)p.in % (4 * lw) != 0 || p.in_pitch % lw != 0))
+      return fail(CT_ECONFIG, "input pointer / pitch not aligned to the load width");
+    if (sw > 1 && ((uintptr_t)p.out % (4 * sw) != 0 || p.out_pitch % sw != 0))
+      return fail(CT_ECONFIG, "output pointer / pitch not aligned to the store width");
+    size_t smem = L.filt_smem ? sizeof(float) * round_up(K * K, 32) : 0;
+    if (staged) {
+      L.tile_w = round_up(c.block_x * c.tile_x + K - 1, 4);
+      L.tile_h = c.block_y * c.tile_y + K - 1;
+      if (c.staging == CT_STAGE_TMA) {
+        if (L.tile_w > 256 || L.tile_h > 256)
+          return fail(CT_ECONFIG, "TMA box wider or taller than 256 elements");
+        if ((uintptr_t)p.in % 16 != 0 || (p.in_pitch * 4) % 16 != 0)
+          return fail(CT_ECONFIG, "TMA needs a 16-byte aligned input and row stride");
+        L.smem_pitch = L.tile_w;
+      } else {
+        L.smem_pitch = L.tile_w;
+        // half-warp rows of 16 lanes reading 4-byte words: put consecutive
+        // tile rows 16 banks apart
+        if (c.block_x == 16 && c.tile_x == 1)
+          while (L.smem_pitch % 32 != 16) L.smem_pitch += 4;
+      }
+      smem += sizeof(float) * (size_t)L.tile_h * L.smem_pitch;
+      if (c.staging == CT_STAGE_TMA) smem += 16;  // mbarrier
+    }
+    L.smem_bytes = smem;
+  }
+  if (plan->grid.y > 65535u) return fail(CT_ECONFIG, "grid y exceeds 65535");
+
+  // device-dependent checks
+  int err = CT_OK;
+  DeviceState* st = current_state(nullptr, &err);
+  if (!st) return fail(err, "no CUDA device");
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, plan->fn);
+  if (e != cudaSuccess) return fail(cuda_status(e), "cudaFuncGetAttributes failed");
+  if (c.block_x * c.block_y > fa.maxThreadsPerBlock)
+    return fail(CT_ECONFIG, "block larger than the kernel's register budget allows");
+  if (L.smem_bytes + fa.sharedSizeBytes > (size_t)st->smem_optin)
+    return fail(CT_ECONFIG, "shared memory exceeds the per-block limit");
+  if (c.staging == CT_STAGE_TMA && specialised && !tensor_map_encoder())
+    return fail(CT_ENOTSUP, "cuTensorMapEncodeTiled unavailable");
+  return CT_OK;
+}
+
+int launch_plan(ConvPlan& plan, cudaStream_t s) {
+  if (plan.empty) return CT_OK;
+  int err = CT_OK;
+  DeviceState* st = current_state(nullptr, &err);
+  if (!st) return err;
+  unsigned* status = device_status_word(&err);
+  if (!status) return err;
+  ConvLaunch& L = plan.L;
+  L.status = status;
+  if (L.smem_bytes > 48 * 1024) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(plan.fn, L.smem_bytes);
+    if (!st->smem_attr_set.count(key)) {
+      cudaError_t e = cudaFuncSetAttribute(plan.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)L.smem_bytes);
+      if (e != cudaSuccess) return cuda_status(e);
+      st->smem_attr_set.insert(key);
+    }
+  }
+  L.tmap = nullptr;
+  if (plan.specialised && L.staging == kStageTma) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return CT_ENOTSUP;
+    const cuuint64_t dims[2] = {(cuuint64_t)L.in_w, (cuuint64_t)L.in_h};
+    const cuuint64_t strides[1] = {(cuuint64_t)L.in_pitch * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)L.tile_w, (cuuint32_t)L.tile_h};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&plan.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)L.in, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return CT_ECONFIG;
+    L.tmap = &plan.tmap;
+  }
+  cudaError_t e;
+  if (plan.specialised) {
+    KernelLauncher fn = launcher_for(L.fh);
+    if (!fn) return CT_ECONFIG;
+    e = fn(L, s);
+  } else {
+    e = launch_generic(L, s);
+  }
+  return cuda_status(e);
+}
+
+}  // namespace convtune
+
+using namespace convtune;
+
+extern "C" {
+
+const char* ct_strerror(int status) {
+  switch (status) {
+    case CT_OK: return "ok";
+    case CT_EINVAL: return "invalid argument";
+    case CT_ENOTSUP: return "not supported on this device or driver";
+    case CT_EPERM: return "clock control not permitted";
+    case CT_ECUDA: return "CUDA call failed";
+    case CT_ENOMEM: return "capacity too small or allocation failed";
+    case CT_ETIMEOUT: return "bounded device wait gave up";
+    case CT_ECONFIG: return "configuration invalid for this problem or device";
+    case CT_EIO: return "results cache I/O failed";
+    default: return "unknown status";
+  }
+}
+
+const char* ct_version(void) { return "convtune 0.1 sm_103a"; }
+
+int ct_conv2d_check(const ct_problem* p, const ct_config* c, char* why, int why_cap) {
+  if (!p || !c) return CT_EINVAL;
+  ConvPlan plan;
+  std::string w;
+  const int rc = plan_conv(*p, *c, &plan, &w);
+  if (why && why_cap > 0) {
+    snprintf(why, (size_t)why_cap, "%s", rc == CT_OK ? "" : w.c_str());
+  }
+  return rc;
+}
+
+int ct_conv2d_run(const ct_problem* p, const ct_config* c, void* stream) {
+  if (!p || !c) return CT_EINVAL;
+  ConvPlan plan;
+  const int rc = plan_conv(*p, *c, &plan, nullptr);
+  if (rc != CT_OK) return rc;
+  return launch_plan(plan, (cudaStream_t)stream);
+}
+
+int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
+                       float* out_host, long out_pitch, int out_h, int out_w, const ct_config* c,
+                       void* stream) {
+  if (!c || !filt) return CT_EINVAL;
+  if (out_h < 0 || out_w < 0 || fh < 1 || fw < 1) return CT_EINVAL;
+  if (out_h == 0 || out_w == 0) return CT_OK;
+  if (!in_host || !out_host) return CT_EINVAL;
+  if (in_pitch < (long)out_w + fw - 1 || out_pitch < out_w) return CT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  int err = CT_OK;
+  DeviceState* st = current_state(nullptr, &err);
+  if (!st) return err;
+  const size_t in_bytes = sizeof(float) * (size_t)(out_h + fh - 1) * (size_t)in_pitch;
+  const size_t out_bytes = sizeof(float) * (size_t)out_h * (size_t)out_pitch;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (st->din_bytes < in_bytes) {
+    if (st->din) cudaFree(st->din);
+    st->din = nullptr;
+    st->din_bytes = 0;
+    if ((e = cudaMalloc(&st->din, in_bytes)) != cudaSuccess) return cuda_status(e);
+    st->din_bytes = in_bytes;
+  }
+  if (st->dout_bytes < out_bytes) {
+    if (st->dout) cudaFree(st->dout);
+    st->dout = nullptr;
+    st->dout_bytes = 0;
+    if ((e = cudaMalloc(&st->dout, out_bytes)) != cudaSuccess) return cuda_status(e);
+    st->dout_bytes = out_bytes;
+  }
+  if ((e = cudaMemcpyAsync(st->din, in_host, in_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  ct_problem p;
+  p.in = st->din;
+  p.in_pitch = in_pitch;
+  p.filt = filt;
+  p.fh = fh;
+  p.fw = fw;
+  p.out = st->dout;
+  p.out_pitch = out_pitch;
+  p.out_h = out_h;
+  p.out_w = out_w;
+  int rc = ct_conv2d_run(&p, c, stream);
+  if (rc != CT_OK) {
+    cudaStreamSynchronize(s);
+    return rc;
+  }
+  if ((e = cudaMemcpyAsync(out_host, st->dout, out_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_status(e);
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int ct_status_read(unsigned* bits, int clear) {
+  if (!bits) return CT_EINVAL;
+  int err = CT_OK;
+  unsigned* st = device_status_word(&err);
+  if (!st) return err;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(bits, st, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(st, 0, sizeof(unsigned));
+  return cuda_status(e);
+}
+
+int ct_device_info_get(ct_device_info* out) {
+  if (!out) return CT_EINVAL;
+  memset(out, 0, sizeof(*out));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  out->sm_count = prop.multiProcessorCount;
+  out->cc_major = prop.major;
+  out->cc_minor = prop.minor;
+  out->max_smem_optin_bytes = (int)prop.sharedMemPerBlockOptin;
+  out->l2_bytes = prop.l2CacheSize;
+  snprintf(out->name, sizeof(out->name), "%s", prop.name);
+  int khz = 0;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) == cudaSuccess)
+    out->sm_clock_max_mhz = khz / 1000.0;
+  else
+    cudaGetLastError();
+  return CT_OK;
+}
+
+}  // extern "C"

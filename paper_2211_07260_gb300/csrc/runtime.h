@@ -1,0 +1,46 @@
+// Internal runtime of libconvtune: problem / configuration validation, the
+// launch plan of one correlation, and per-device scratch.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/convtune.h"
+#include "conv2d_launch.h"
+
+namespace convtune {
+
+// Everything needed to launch one correlation, resolved from (problem,
+// config) by plan_conv().
+struct ConvPlan {
+  ConvLaunch L{};
+  bool specialised = false;  // square odd filter <= 17
+  bool empty = false;        // out_h == 0 or out_w == 0: nothing to launch
+  const void* fn = nullptr;  // kernel function
+  dim3 grid, block;
+  CUtensorMap tmap;          // filled when staging == TMA
+};
+
+// Validate and resolve; returns CT_OK / CT_EINVAL / CT_ECONFIG / CT_ENOTSUP /
+// CT_ECUDA.  `why` receives a reason when not OK.
+int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::string* why);
+
+// Launch a resolved plan on a stream.
+int launch_plan(ConvPlan& plan, cudaStream_t s);
+
+// Device status word of the current device (allocated on first use).
+unsigned* device_status_word(int* err);
+
+// Map a CUDA error to a status code (and remember its text for ct_strerror
+// callers that want detail).
+int cuda_status(cudaError_t e);
+
+// Useful work of one correlation: 2 * fh * fw * out_h * out_w FLOP.
+double conv_flop(const ct_problem& p);
+// Algorithmic bytes of one correlation: padded input read once, output
+// written once, taps once.
+double conv_bytes(const ct_problem& p);
+
+}  // namespace convtune

@@ -1,0 +1,63 @@
+"""The C ABI library loads on a CPU-only host and exports every function that
+include/*.h declares; host-side argument checks answer without a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2211_07260_gb300 import api
+from paper_2211_07260_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(ct_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return api.lib()
+
+
+def test_header_declares_functions():
+    names = declared_functions()
+    assert "ct_conv2d_run" in names and "ct_strerror" in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_version(lib):
+    assert api.strerror(api.CT_OK) == "ok"
+    assert "configuration" in api.strerror(api.CT_ECONFIG)
+    assert api.strerror(12345) == "unknown status"
+    assert api.version().startswith("convtune")
+
+
+def test_host_side_argument_checks_need_no_gpu(lib):
+    assert lib.ct_conv2d_run(None, None, None) == api.CT_EINVAL
+    c = api.Config().to_c()
+    p = api.CtProblem(0, 0, 0, 3, 3, 0, 0, 4, 4)  # null filter
+    assert lib.ct_conv2d_check(ctypes.byref(p), ctypes.byref(c), None, 0) == api.CT_EINVAL
+    taps = (ctypes.c_float * 9)()
+    p = api.CtProblem(0, 0, ctypes.addressof(taps), 3, 3, 0, 0, 0, 4)  # empty: nothing to do
+    assert lib.ct_conv2d_run(ctypes.byref(p), ctypes.byref(c), None) == api.CT_OK
+    p = api.CtProblem(16, 9, ctypes.addressof(taps), 3, 3, 32, 8, 4, 8)  # pitch too small
+    why = ctypes.create_string_buffer(128)
+    assert lib.ct_conv2d_check(ctypes.byref(p), ctypes.byref(c), why, 128) == api.CT_EINVAL
+    assert b"in_pitch" in why.value
+    bad = api.Config(block_x=48).to_c()
+    p = api.CtProblem(16, 12, ctypes.addressof(taps), 3, 3, 32, 8, 4, 8)
+    assert lib.ct_conv2d_check(ctypes.byref(p), ctypes.byref(bad), None, 0) == api.CT_ECONFIG
