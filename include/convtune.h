@@ -148,6 +148,250 @@ typedef struct {
 } ct_device_info;
 int ct_device_info_get(ct_device_info* out);
 
+
+/* ---- platform: energy counter, sensors, clock control ------------------- */
+
+/*
+ * Energy comes from the device's total-energy counter (NVML,
+ * millijoules since driver load); power, SM clock, throttle reasons,
+ * temperature and other compute processes are read beside it (the sensors
+ * the paper's NVML observer records, Section III-B).  The default table is
+ * backed by libnvidia-ml, loaded at run time; a caller (tests, simulations)
+ * may install its own table.  Every function returns CT_OK or a CT_E*
+ * status; a NULL member means "not available" (CT_ENOTSUP).
+ *
+ * Clock control (the paper's nvml_gr_clock tunable, Section III-C) changes
+ * a device setting that outlives the process.  The NVML table refuses it
+ * (CT_EPERM) unless the environment variable CONVTUNE_ALLOW_CLOCK_CONTROL
+ * is "1"; when enabled, every lock is undone on return, on error and at exit.
+ */
+enum { CT_UNIT_CONV = 0, CT_UNIT_FMA = 1, CT_UNIT_COPY = 2 };
+/* Throttle-reason bits (same values as NVML's clocks-event reasons). */
+enum { CT_THR_SW_POWER_CAP = 0x4, CT_THR_HW_SLOWDOWN = 0x8, CT_THR_SW_THERMAL = 0x20,
+       CT_THR_HW_THERMAL = 0x40, CT_THR_HW_POWER_BRAKE = 0x80 };
+typedef struct {
+  void* ctx;
+  int (*energy_mj)(void* ctx, unsigned long long* mj);
+  int (*power_mw)(void* ctx, unsigned* mw);
+  int (*sm_clock_mhz)(void* ctx, unsigned* mhz);
+  int (*throttle_reasons)(void* ctx, unsigned long long* bits);
+  int (*temperature_c)(void* ctx, unsigned* c);
+  int (*other_processes)(void* ctx, int* n);
+  int (*supported_sm_clocks)(void* ctx, int* mhz, int cap, int* n); /* descending */
+  int (*lock_sm_clock)(void* ctx, int mhz);
+  int (*reset_sm_clock)(void* ctx);
+  double (*now_s)(void* ctx);  /* monotonic seconds; NULL: host steady clock */
+  /* Simulation hook.  NULL: launches run on the GPU.  Otherwise the
+     measurement calls this instead of launching: "run n launches of unit
+     `kind` (CT_UNIT_*; cfg is the configuration for CT_UNIT_CONV, else NULL)
+     and report their device time in *elapsed_ms". */
+  int (*run_launches)(void* ctx, int kind, const ct_config* cfg, int n, double* elapsed_ms);
+} ct_platform_ops;
+
+/* Install a platform table (copied); NULL restores the NVML table. */
+int ct_set_platform_ops(const ct_platform_ops* ops);
+/* CT_OK if the NVML table found libnvidia-ml and the current device. */
+int ct_nvml_status(void);
+/* Supported SM clocks of the current device, descending (MHz). */
+int ct_supported_sm_clocks(int* mhz, int cap, int* n);
+/* Lock / unlock the SM clock through the current table (see above). */
+int ct_lock_sm_clock(int mhz);
+int ct_reset_sm_clock(void);
+
+/* ---- measurement of one point ------------------------------------------ */
+
+typedef struct {
+  double window_s;  /* energy window: mean power between two energy-counter
+                       updates at least this far apart; <= 0 -> 1.0 s (the
+                       paper's default observation time, Section III-B)   */
+  double warmup_s;  /* continuous load before the window opens; < 0 -> 0.2 */
+  double graph_ms;  /* target device time of one replayed CUDA graph of
+                       back-to-back launches; <= 0 -> 2.0                  */
+  int time_only;    /* 1: time the launches only, no energy window         */
+  int time_reps;    /* graph replays timed when time_only; <= 0 -> 5       */
+} ct_measure_options;
+
+/* Record flags. */
+enum { CT_REC_THROTTLED = 1,      /* a throttle reason was active           */
+       CT_REC_COTENANT = 2,       /* another compute process was on the GPU */
+       CT_REC_DEFAULT_CLOCKS = 4, /* clock requested but not locked         */
+       CT_REC_INVALID = 8,        /* configuration pruned (not measured)    */
+       CT_REC_CACHED = 16,        /* taken from the results cache           */
+       CT_REC_NO_ENERGY = 32,     /* no energy counter: energy from power   */
+       CT_REC_IDLE_GAPS = 64 };   /* the device idled inside the window     */
+
+/* One measured point (the paper's observer record plus its metrics). */
+typedef struct {
+  ct_config cfg;
+  int clock_mhz_req;       /* requested SM clock, 0 = default clocks        */
+  double clock_mhz_meas;   /* median SM clock read during the window        */
+  double t_s;              /* device time per launch (CUDA events)          */
+  double energy_j;         /* energy per launch = mean power x t_s          */
+  double power_w_mean;     /* energy-counter difference / window time       */
+  double power_w_median;   /* median power reading in the window            */
+  double energy_j_median_power; /* Section III-A estimate: median P x t_s   */
+  double gflops;           /* useful GFLOP per launch / t_s                 */
+  double gflops_per_j;     /* useful GFLOP per launch / energy_j            */
+  double temp_c;           /* highest temperature read in the window        */
+  double wall_s;           /* host seconds spent on this point              */
+  int n_launches;          /* launches timed                                */
+  int flags;               /* CT_REC_*                                      */
+} ct_record;
+
+/*
+ * Measure one configuration: build a CUDA graph of back-to-back launches on
+ * a private stream ordered after `stream`, warm up, then replay it while
+ * reading the energy counter.  The energy window opens at one counter update
+ * and closes at the first update at least window_s later, with the device
+ * busy throughout; mean power over the window times the event-timed time per
+ * launch gives the energy per launch.  Synchronises before returning.
+ * Errors: as ct_conv2d_run; CT_ECONFIG leaves out->flags = CT_REC_INVALID.
+ */
+int ct_measure_conv(const ct_problem* p, const ct_config* c, const ct_measure_options* opt,
+                    void* stream, ct_record* out);
+
+
+/* ---- power model and steered clock range (Section IV-E) ----------------- */
+
+/*
+ * Eq. (powercurve): P*(f) = min(P_max, P_idle + alpha * f * v(f)^2), f in
+ * GHz.  Without a voltage readout v(f) = 1 + beta * max(0, f - tau) (the
+ * paper's estimate, read as continuous at the ridge point tau).
+ * alpha: W/GHz (estimated v) or W/(GHz V^2) (measured v); beta: per GHz.
+ */
+typedef struct {
+  double p_idle_w, alpha, beta, tau_mhz, p_max_w;
+  int has_voltage;       /* 1: fitted with measured voltages               */
+  double sse;            /* residual sum of squares of the kept samples    */
+  int n_used;            /* samples kept (not throttled)                   */
+  double f_lo_mhz;       /* lowest kept sample clock                       */
+  double f_thr_mhz;      /* highest kept sample clock (before throttling)  */
+  double f_opt_mhz;      /* clock minimising P*(f)/f on [f_lo, f_thr]      */
+} ct_power_model;
+
+/*
+ * Fit the model to n samples (f_mhz[i], p_w[i]) with optional voltages and
+ * throttle flags (flagged samples are dropped).  With voltages the fit is
+ * linear least squares in x = f v^2; without, tau runs over the integer-MHz
+ * grid of the kept clock range (needing two kept samples above it) and
+ * (P_idle, alpha, beta >= 0) are fitted by Levenberg-Marquardt at each grid
+ * point; the least residual wins, ties (1e-12 relative) keep the lower tau.
+ * p_max_w <= 0 takes the largest measured power.  Needs >= 3 kept samples
+ * (CT_EINVAL otherwise).  Host only; no GPU needed.
+ */
+int ct_fit_power_model(const double* f_mhz, const double* p_w, const double* v_or_null,
+                       const int* throttled_or_null, int n, double p_max_w,
+                       ct_power_model* out);
+/* P*(f) of an estimated-voltage model at n clocks (MHz). */
+int ct_model_power(const ct_power_model* m, const double* f_mhz, int n, double* p_w);
+/* Clock minimising P*(f)/f over [f_lo, f_thr] (energy per cycle). */
+int ct_optimal_clock(const ct_power_model* m, double* f_opt_mhz);
+/*
+ * Supported clocks c with (1-rel)*c0 <= c <= (1+rel)*c0, ascending, where c0
+ * is the model optimum (center 0) or tau, the ridge point (center 1); an
+ * empty window yields the nearest supported clock (ties: lower).  *n_out is
+ * the count; CT_ENOMEM if it exceeds cap.
+ */
+int ct_pick_clock_range(const ct_power_model* m, const int* supported_mhz, int n_supported,
+                        double rel_halfwidth, int center, int* out_mhz, int cap, int* n_out,
+                        double* center_mhz);
+
+/* ---- tuning (Sections III-C and IV) ------------------------------------- */
+
+enum { CT_OBJ_TIME = 0, CT_OBJ_ENERGY = 1, CT_OBJ_GFLOPS_PER_W = 2 };
+/* Built-in spaces, in lexicographic order block_x, block_y, tile_x, tile_y,
+   staging, filter_mem, vec_width:
+   CT_SPACE_BASIC  block_x {16,32,64,128} x block_y {1,2,4,8} x tile_x, tile_y
+                   {1,2,4} x staging {direct, smem}; constant filter, vector
+                   width 4 (288 points);
+   CT_SPACE_FULL   ... x staging {direct, smem, tma} x filter {shared, const}
+                   x vector width {1,2,4} (2592 points). */
+enum { CT_SPACE_BASIC = 0, CT_SPACE_FULL = 1 };
+int ct_space(int which, ct_config* out, int cap, int* n);
+
+typedef struct {
+  int objective;                /* CT_OBJ_*                                 */
+  ct_measure_options measure;   /* per-point measurement                    */
+  const char* cache_path;       /* JSON-lines results cache; NULL: none     */
+  double settle_s;              /* wait after each clock change             */
+  int fallback_default_clocks;  /* 1: if locking is refused, measure once at
+                                   default clocks (records flagged) instead
+                                   of returning CT_EPERM                    */
+} ct_tune_options;
+
+/*
+ * Exhaustive search of `space` (NULL: CT_SPACE_BASIC) x `clocks` (NULL or
+ * n_clocks = 0: default clocks, no locking), clock-major so each clock is
+ * locked once.  Invalid points are recorded with CT_REC_INVALID; cached
+ * points (same device, problem, configuration, clock and window) are reused
+ * and flagged CT_REC_CACHED; new points are appended to the cache as they are
+ * measured, so an interrupted sweep resumes.  The clock is reset before
+ * returning, on every path.  records[] receives n_space x max(1, n_clocks)
+ * records in sweep order (CT_ENOMEM and *n_records = needed if cap is too
+ * small; with fallback_default_clocks and a refused lock, one default-clock
+ * pass of n_space records, flagged CT_REC_DEFAULT_CLOCKS); *best_index is the objective's optimum among valid records (ties:
+ * shorter time, lower clock, lexicographically smaller configuration), or
+ * -1.
+ */
+int ct_tune(const ct_problem* p, const ct_config* space, int n_space, const int* clocks_mhz,
+            int n_clocks, const ct_tune_options* opt, void* stream, ct_record* records, int cap,
+            int* n_records, int* best_index);
+
+/* The selection rule of ct_tune over given records, optionally restricted to
+   records whose requested clock is in clocks[] (n_clocks > 0). */
+int ct_select_best(const ct_record* recs, int n, int objective, const int* clocks,
+                   int n_clocks, int* best_index);
+
+
+/* ---- microbenchmarks for the fit (Section IV-E) ------------------------- */
+
+/*
+ * CT_UNIT_FMA: a full-load FP32 kernel, 8 independent fmaf chains per
+ * thread in registers (~1e9 FMAs per launch, 4 CTAs of 256 threads per SM;
+ * *work = exact FLOP).  CT_UNIT_COPY: a 1 GiB float4 device-to-device copy
+ * (*work = 2^31 bytes moved).  Their buffers are library scratch (2 GiB for
+ * the copy), allocated on first use and freed by ct_microbench_release().
+ */
+int ct_microbench_launch(int which, void* stream, double* work);
+/* Measure one microbenchmark at the current clocks (as ct_measure_conv). */
+int ct_measure_microbench(int which, const ct_measure_options* opt, void* stream,
+                          ct_record* out);
+/*
+ * Power samples for the fit: for each clock (locked in turn; NULL / 0
+ * clocks: one sample at default clocks) measure the microbenchmark and
+ * report the median SM clock, the mean power of the energy window (median
+ * reading if the counter is absent) and whether it throttled (a throttle
+ * reason, or the clock not held).  CT_EPERM if a lock is refused.
+ */
+int ct_measure_power_samples(int which, const int* clocks_mhz, int n_clocks,
+                             const ct_measure_options* opt, void* stream, double* f_meas_mhz,
+                             double* p_w, int* throttled, ct_record* recs_or_null);
+int ct_microbench_release(void);
+
+/* Result of the model-steered search. */
+typedef struct {
+  ct_power_model model;  /* fitted on the microbenchmark sweep              */
+  double center_mhz;     /* model optimum the clock range is centred on     */
+  int n_range;           /* clocks in the steered range                     */
+  double fit_wall_s;     /* host seconds: microbenchmark sweep + fit        */
+  double tune_wall_s;    /* host seconds: the steered sweep                 */
+} ct_steer_result;
+
+/*
+ * Model-steered tuning (Section IV-E): sweep the microbenchmark `which_bench`
+ * over fit_clocks (>= 3), fit the power model (f = the locked clocks), take
+ * the supported clocks (NULL: the platform's list) within +-rel_halfwidth of
+ * the predicted optimum and run ct_tune over that range only.  records /
+ * n_records / best_index as ct_tune; range_out (optional) receives the
+ * range.
+ */
+int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
+                    const int* fit_clocks, int n_fit_clocks, const int* supported,
+                    int n_supported, double rel_halfwidth, int which_bench,
+                    const ct_tune_options* opt, void* stream, ct_steer_result* res,
+                    int* range_out, int range_cap, ct_record* records, int cap, int* n_records,
+                    int* best_index);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,8 +30,11 @@ Readings taken where the paper is silent or garbled:
   (projected), from four starts: the beta = 0 closed form and
   beta0 in {0.1, 1, 10} per GHz with (P_idle, alpha) the linear least-squares
   solution at that beta0.  LM stops when the relative step is below 1e-15 or
-  after 500 iterations.  The tau with the least residual wins; residuals within
-  1e-12 relative count as a tie and the smaller tau is kept.  A tau needs at
+  after 500 iterations, or when no step lowers the residual; Gauss-Newton
+  steps (LM with lambda = 0) then continue while they contract, because the
+  residual's last bits cannot resolve the parameters beyond ~sqrt(eps).
+  The tau with the least residual wins; residuals within 1e-12 relative
+  count as a tie and the smaller tau is kept.  A tau needs at
   least two kept samples strictly above it.
 * P_max is not fitted: the caller's value, else the largest measured power
   over all samples (throttled ones included), used only in prediction.
@@ -124,6 +127,41 @@ def _levenberg_marquardt(theta0, f, d, p):
     return theta, s
 
 
+def _gauss_newton_polish(theta, f, d, p):
+    """Continue the iteration with lambda = 0 while the steps contract.
+
+    Near the minimum the residual sum S changes by less than its rounding
+    error long before the parameters settle (S - S* ~ step^2), so the
+    LM acceptance test (S must decrease) stops at ~sqrt(eps) relative
+    accuracy.  Gauss-Newton steps are driven by the gradient J^T r, which
+    stays accurate; iterating them while they shrink converges to the
+    stationary point.  beta stays at 0 when the bound is active.
+    """
+    theta = np.array(theta, dtype=np.float64)
+    last = np.inf
+    for _ in range(100):
+        r = p - _model(theta, f, d)
+        jac = _jacobian(theta, f, d)
+        free = [0, 1] if theta[2] == 0.0 else [0, 1, 2]
+        jf = jac[:, free]
+        try:
+            delta = np.linalg.solve(jf.T @ jf, jf.T @ r)
+        except np.linalg.LinAlgError:
+            break
+        size = float(np.linalg.norm(delta))
+        if not size < last:
+            break
+        cand = theta.copy()
+        cand[free] += delta
+        if cand[2] < 0.0:
+            break
+        theta, last = cand, size
+        if size <= LM_STEP_TOL * max(float(np.linalg.norm(theta)), 1e-300):
+            break
+    r = p - _model(theta, f, d)
+    return theta, float(r @ r)
+
+
 def _fit_fixed_tau(f, d, p):
     best = None
     starts = []
@@ -135,6 +173,7 @@ def _fit_fixed_tau(f, d, p):
         starts.append((a, b, beta0))
     for st in starts:
         theta, s = _levenberg_marquardt(st, f, d, p)
+        theta, s = _gauss_newton_polish(theta, f, d, p)
         if best is None or s < best[1]:
             best = (theta, s)
     return best

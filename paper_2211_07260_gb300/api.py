@@ -43,6 +43,79 @@ class CtDeviceInfo(ctypes.Structure):
                 ("sm_clock_max_mhz", c_double), ("name", ctypes.c_char * 96)]
 
 
+CT_UNIT_CONV, CT_UNIT_FMA, CT_UNIT_COPY = 0, 1, 2
+CT_OBJ_TIME, CT_OBJ_ENERGY, CT_OBJ_GFLOPS_PER_W = 0, 1, 2
+CT_SPACE_BASIC, CT_SPACE_FULL = 0, 1
+REC_THROTTLED, REC_COTENANT, REC_DEFAULT_CLOCKS, REC_INVALID, REC_CACHED, REC_NO_ENERGY, \
+    REC_IDLE_GAPS = 1, 2, 4, 8, 16, 32, 64
+OBJECTIVES = {"time": CT_OBJ_TIME, "energy": CT_OBJ_ENERGY, "gflops_per_w": CT_OBJ_GFLOPS_PER_W}
+
+c_uint, c_ulonglong = ctypes.c_uint, ctypes.c_ulonglong
+_FN_ULL = ctypes.CFUNCTYPE(c_int, c_void_p, ctypes.POINTER(c_ulonglong))
+_FN_UINT = ctypes.CFUNCTYPE(c_int, c_void_p, ctypes.POINTER(c_uint))
+_FN_INTP = ctypes.CFUNCTYPE(c_int, c_void_p, ctypes.POINTER(c_int))
+_FN_CLOCKS = ctypes.CFUNCTYPE(c_int, c_void_p, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int))
+_FN_LOCK = ctypes.CFUNCTYPE(c_int, c_void_p, c_int)
+_FN_RESET = ctypes.CFUNCTYPE(c_int, c_void_p)
+_FN_NOW = ctypes.CFUNCTYPE(c_double, c_void_p)
+_FN_RUN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int, ctypes.POINTER(CtConfig), c_int,
+                           ctypes.POINTER(c_double))
+
+
+class CtPlatformOps(ctypes.Structure):
+    _fields_ = [("ctx", c_void_p), ("energy_mj", _FN_ULL), ("power_mw", _FN_UINT),
+                ("sm_clock_mhz", _FN_UINT), ("throttle_reasons", _FN_ULL),
+                ("temperature_c", _FN_UINT), ("other_processes", _FN_INTP),
+                ("supported_sm_clocks", _FN_CLOCKS), ("lock_sm_clock", _FN_LOCK),
+                ("reset_sm_clock", _FN_RESET), ("now_s", _FN_NOW), ("run_launches", _FN_RUN)]
+
+
+class CtMeasureOptions(ctypes.Structure):
+    _fields_ = [("window_s", c_double), ("warmup_s", c_double), ("graph_ms", c_double),
+                ("time_only", c_int), ("time_reps", c_int)]
+
+
+class CtRecord(ctypes.Structure):
+    _fields_ = [("cfg", CtConfig), ("clock_mhz_req", c_int), ("clock_mhz_meas", c_double),
+                ("t_s", c_double), ("energy_j", c_double), ("power_w_mean", c_double),
+                ("power_w_median", c_double), ("energy_j_median_power", c_double),
+                ("gflops", c_double), ("gflops_per_j", c_double), ("temp_c", c_double),
+                ("wall_s", c_double), ("n_launches", c_int), ("flags", c_int)]
+
+    def to_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cfg"}
+        d["cfg"] = Config.from_c(self.cfg).as_tuple()
+        return d
+
+
+class CtPowerModel(ctypes.Structure):
+    _fields_ = [("p_idle_w", c_double), ("alpha", c_double), ("beta", c_double),
+                ("tau_mhz", c_double), ("p_max_w", c_double), ("has_voltage", c_int),
+                ("sse", c_double), ("n_used", c_int), ("f_lo_mhz", c_double),
+                ("f_thr_mhz", c_double), ("f_opt_mhz", c_double)]
+
+    def to_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "CtPowerModel":
+        m = cls()
+        for k, _ in cls._fields_:
+            if k in d:
+                setattr(m, k, d[k])
+        return m
+
+
+class CtTuneOptions(ctypes.Structure):
+    _fields_ = [("objective", c_int), ("measure", CtMeasureOptions), ("cache_path", ctypes.c_char_p),
+                ("settle_s", c_double), ("fallback_default_clocks", c_int)]
+
+
+class CtSteerResult(ctypes.Structure):
+    _fields_ = [("model", CtPowerModel), ("center_mhz", c_double), ("n_range", c_int),
+                ("fit_wall_s", c_double), ("tune_wall_s", c_double)]
+
+
 class ConvTuneError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -83,6 +156,30 @@ _SIGS = {
                                    c_int, c_int, c_void_p, c_void_p]),
     "ct_status_read": (c_int, [ctypes.POINTER(ctypes.c_uint), c_int]),
     "ct_device_info_get": (c_int, [c_void_p]),
+    "ct_set_platform_ops": (c_int, [c_void_p]),
+    "ct_nvml_status": (c_int, []),
+    "ct_supported_sm_clocks": (c_int, [c_void_p, c_int, c_void_p]),
+    "ct_lock_sm_clock": (c_int, [c_int]),
+    "ct_reset_sm_clock": (c_int, []),
+    "ct_measure_conv": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ct_fit_power_model": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double,
+                                   c_void_p]),
+    "ct_model_power": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    "ct_optimal_clock": (c_int, [c_void_p, c_void_p]),
+    "ct_pick_clock_range": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_int,
+                                    c_void_p, c_void_p]),
+    "ct_space": (c_int, [c_int, c_void_p, c_int, c_void_p]),
+    "ct_tune": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                        c_int, c_void_p, c_void_p]),
+    "ct_select_best": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_void_p]),
+    "ct_microbench_launch": (c_int, [c_int, c_void_p, c_void_p]),
+    "ct_measure_microbench": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
+    "ct_measure_power_samples": (c_int, [c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p]),
+    "ct_microbench_release": (c_int, []),
+    "ct_tune_steered": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
+                                c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                c_void_p, c_int, c_void_p, c_void_p]),
 }
 
 
@@ -216,3 +313,204 @@ def device_info() -> dict:
     return dict(sm_count=d.sm_count, cc=(d.cc_major, d.cc_minor),
                 max_smem_optin_bytes=d.max_smem_optin_bytes, l2_bytes=d.l2_bytes,
                 sm_clock_max_mhz=d.sm_clock_max_mhz, name=d.name.decode())
+
+
+# ---- platform ---------------------------------------------------------------
+_platform_keepalive = None
+
+
+def set_platform_ops(ops: "CtPlatformOps | None"):
+    """Install a platform table (None restores NVML).  The Python callbacks
+    are kept alive until the next call."""
+    global _platform_keepalive
+    _check(lib().ct_set_platform_ops(ctypes.byref(ops) if ops is not None else None),
+           "ct_set_platform_ops")
+    _platform_keepalive = ops
+
+
+def nvml_status() -> int:
+    return int(lib().ct_nvml_status())
+
+
+def supported_sm_clocks() -> list:
+    buf = (c_int * 1024)()
+    n = c_int(0)
+    _check(lib().ct_supported_sm_clocks(buf, 1024, ctypes.byref(n)), "ct_supported_sm_clocks")
+    return [buf[i] for i in range(n.value)]
+
+
+def measure_options(window_s=1.0, warmup_s=0.2, graph_ms=2.0, time_only=False, time_reps=5):
+    return CtMeasureOptions(window_s, warmup_s, graph_ms, int(bool(time_only)), time_reps)
+
+
+def measure_conv(inp, filt, out, out_h, out_w, cfg: Config, opts=None, stream=None):
+    p, f = make_problem(inp, filt, out, out_h, out_w)
+    c = cfg.to_c()
+    r = CtRecord()
+    o = opts or measure_options()
+    _check(lib().ct_measure_conv(ctypes.byref(p), ctypes.byref(c), ctypes.byref(o),
+                                 c_void_p(stream_handle(stream)), ctypes.byref(r)),
+           "ct_measure_conv")
+    return r.to_dict()
+
+
+# ---- power model ------------------------------------------------------------
+def _darr(x):
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a, a.ctypes.data
+
+
+def fit_power_model(f_mhz, p_w, v=None, throttled=None, p_max_w=0.0) -> dict:
+    f, fp = _darr(f_mhz)
+    p, pp = _darr(p_w)
+    vv, vp = _darr(v) if v is not None else (None, None)
+    t = np.ascontiguousarray(throttled, dtype=np.int32) if throttled is not None else None
+    m = CtPowerModel()
+    _check(lib().ct_fit_power_model(fp, pp, vp, t.ctypes.data if t is not None else None, f.size,
+                                    float(p_max_w or 0.0), ctypes.byref(m)), "ct_fit_power_model")
+    return m.to_dict()
+
+
+def model_power(model: dict, f_mhz):
+    f, fp = _darr(f_mhz)
+    out = np.empty_like(f)
+    m = CtPowerModel.from_dict(model)
+    _check(lib().ct_model_power(ctypes.byref(m), fp, f.size, out.ctypes.data), "ct_model_power")
+    return out
+
+
+def optimal_clock(model: dict) -> float:
+    m = CtPowerModel.from_dict(model)
+    v = c_double(0)
+    _check(lib().ct_optimal_clock(ctypes.byref(m), ctypes.byref(v)), "ct_optimal_clock")
+    return v.value
+
+
+def pick_clock_range(model: dict, supported_mhz, rel_halfwidth=0.10, center="optimum"):
+    sup = np.ascontiguousarray(supported_mhz, dtype=np.int32)
+    out = np.zeros(max(1, sup.size), dtype=np.int32)
+    n = c_int(0)
+    c0 = c_double(0)
+    m = CtPowerModel.from_dict(model)
+    _check(lib().ct_pick_clock_range(ctypes.byref(m), sup.ctypes.data, sup.size,
+                                     float(rel_halfwidth), 1 if center == "ridge" else 0,
+                                     out.ctypes.data, out.size, ctypes.byref(n),
+                                     ctypes.byref(c0)), "ct_pick_clock_range")
+    return [int(x) for x in out[:n.value]], c0.value
+
+
+# ---- tuning -----------------------------------------------------------------
+def space(which=CT_SPACE_BASIC) -> list:
+    n = c_int(0)
+    lib().ct_space(which, None, 0, ctypes.byref(n))
+    buf = (CtConfig * n.value)()
+    _check(lib().ct_space(which, buf, n.value, ctypes.byref(n)), "ct_space")
+    return [Config.from_c(buf[i]) for i in range(n.value)]
+
+
+def tune_options(objective="energy", window_s=1.0, warmup_s=0.2, graph_ms=2.0, time_only=False,
+                 cache_path=None, settle_s=0.0, fallback_default_clocks=True):
+    obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
+    return CtTuneOptions(obj, measure_options(window_s, warmup_s, graph_ms, time_only),
+                         cache_path.encode() if cache_path else None, settle_s,
+                         int(bool(fallback_default_clocks)))
+
+
+def _space_array(cfgs):
+    if cfgs is None:
+        return None, 0
+    arr = (CtConfig * len(cfgs))(*[c.to_c() for c in cfgs])
+    return arr, len(cfgs)
+
+
+def tune(inp, filt, out, out_h, out_w, cfgs=None, clocks=None, opts=None, stream=None,
+         in_pitch=None, out_pitch=None):
+    """Exhaustive search (ct_tune).  Returns (records, best_index)."""
+    p, f = make_problem(inp, filt, out, out_h, out_w, in_pitch, out_pitch)
+    sp, ns = _space_array(cfgs)
+    ck = np.ascontiguousarray(clocks if clocks is not None else [], dtype=np.int32)
+    o = opts or tune_options()
+    n_space = ns if sp is not None else len(space(CT_SPACE_BASIC))
+    cap = n_space * max(1, ck.size)
+    recs = (CtRecord * cap)()
+    n = c_int(0)
+    best = c_int(-1)
+    _check(lib().ct_tune(ctypes.byref(p), sp, ns, ck.ctypes.data if ck.size else None, ck.size,
+                         ctypes.byref(o), c_void_p(stream_handle(stream)), recs, cap,
+                         ctypes.byref(n), ctypes.byref(best)), "ct_tune")
+    return [recs[i].to_dict() for i in range(n.value)], best.value
+
+
+def select_best(records, objective="energy", clocks=None) -> int:
+    arr = (CtRecord * len(records))()
+    for i, r in enumerate(records):
+        for k, _ in CtRecord._fields_:
+            if k == "cfg":
+                arr[i].cfg = Config(*r["cfg"]).to_c()
+            else:
+                setattr(arr[i], k, r[k])
+    ck = np.ascontiguousarray(clocks if clocks is not None else [], dtype=np.int32)
+    best = c_int(-1)
+    obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
+    _check(lib().ct_select_best(arr, len(records), obj, ck.ctypes.data if ck.size else None,
+                                ck.size, ctypes.byref(best)), "ct_select_best")
+    return best.value
+
+
+def microbench_launch(which: int, stream=None) -> float:
+    w = c_double(0)
+    _check(lib().ct_microbench_launch(which, c_void_p(stream_handle(stream)), ctypes.byref(w)),
+           "ct_microbench_launch")
+    return w.value
+
+
+def measure_microbench(which: int, opts=None, stream=None) -> dict:
+    r = CtRecord()
+    o = opts or measure_options()
+    _check(lib().ct_measure_microbench(which, ctypes.byref(o), c_void_p(stream_handle(stream)),
+                                       ctypes.byref(r)), "ct_measure_microbench")
+    return r.to_dict()
+
+
+def measure_power_samples(which: int, clocks=None, opts=None, stream=None):
+    ck = np.ascontiguousarray(clocks if clocks is not None else [], dtype=np.int32)
+    n = max(1, ck.size)
+    f = np.zeros(n)
+    p = np.zeros(n)
+    t = np.zeros(n, dtype=np.int32)
+    recs = (CtRecord * n)()
+    o = opts or measure_options()
+    _check(lib().ct_measure_power_samples(which, ck.ctypes.data if ck.size else None, ck.size,
+                                          ctypes.byref(o), c_void_p(stream_handle(stream)),
+                                          f.ctypes.data, p.ctypes.data, t.ctypes.data, recs),
+           "ct_measure_power_samples")
+    return f, p, t.astype(bool), [r.to_dict() for r in recs]
+
+
+def tune_steered(inp, filt, out, out_h, out_w, fit_clocks, cfgs=None, supported=None,
+                 rel_halfwidth=0.10, which_bench=CT_UNIT_FMA, opts=None, stream=None,
+                 in_pitch=None, out_pitch=None):
+    """Model-steered search (ct_tune_steered).  Returns (result, range,
+    records, best_index)."""
+    p, f = make_problem(inp, filt, out, out_h, out_w, in_pitch, out_pitch)
+    sp, ns = _space_array(cfgs)
+    fc = np.ascontiguousarray(fit_clocks, dtype=np.int32)
+    su = np.ascontiguousarray(supported if supported is not None else [], dtype=np.int32)
+    n_space = ns if sp is not None else len(space(CT_SPACE_BASIC))
+    rng = np.zeros(1024, dtype=np.int32)
+    cap = n_space * 1024
+    recs = (CtRecord * cap)()
+    res = CtSteerResult()
+    n = c_int(0)
+    best = c_int(-1)
+    o = opts or tune_options()
+    _check(lib().ct_tune_steered(ctypes.byref(p), sp, ns, fc.ctypes.data, fc.size,
+                                 su.ctypes.data if su.size else None, su.size,
+                                 float(rel_halfwidth), which_bench, ctypes.byref(o),
+                                 c_void_p(stream_handle(stream)), ctypes.byref(res),
+                                 rng.ctypes.data, rng.size, recs, cap, ctypes.byref(n),
+                                 ctypes.byref(best)), "ct_tune_steered")
+    result = dict(model=res.model.to_dict(), center_mhz=res.center_mhz, n_range=res.n_range,
+                  fit_wall_s=res.fit_wall_s, tune_wall_s=res.tune_wall_s)
+    return result, [int(x) for x in rng[:res.n_range]], \
+        [recs[i].to_dict() for i in range(n.value)], best.value

@@ -147,7 +147,8 @@ double conv_bytes(const ct_problem& p) {
   return 4.0 * (in_elems + (double)p.out_h * p.out_w + (double)p.fh * p.fw);
 }
 
-int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::string* why) {
+int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::string* why,
+              bool device_checks) {
   auto fail = [&](int code, const char* msg) {
     if (why) *why = msg;
     return code;
@@ -246,6 +247,7 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
   }
   if (plan->grid.y > 65535u) return fail(CT_ECONFIG, "grid y exceeds 65535");
 
+  if (!device_checks) return CT_OK;
   // device-dependent checks
   int err = CT_OK;
   DeviceState* st = current_state(nullptr, &err);

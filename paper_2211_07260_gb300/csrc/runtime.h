@@ -24,8 +24,11 @@ struct ConvPlan {
 };
 
 // Validate and resolve; returns CT_OK / CT_EINVAL / CT_ECONFIG / CT_ENOTSUP /
-// CT_ECUDA.  `why` receives a reason when not OK.
-int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::string* why);
+// CT_ECUDA.  `why` receives a reason when not OK.  device_checks = false
+// skips the checks that need a CUDA device (register and shared-memory
+// limits), for simulated measurement.
+int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::string* why,
+              bool device_checks = true);
 
 // Launch a resolved plan on a stream.
 int launch_plan(ConvPlan& plan, cudaStream_t s);
