@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: FP32 2-D correlation GFLOP/s and GFLOP/J at the tuned
+configuration on GB300 (one JSON line on stdout).
+
+Workload (default): a 4096 x 4096 output, 17 x 17 filter, zero-padded input
+4112 x 4112 uniform[0, 1) (seed 1), filter uniform[0, 1) normalised to sum 1,
+at the configuration the energy-objective tuner picked (tuned_configs.json),
+default clocks.  A step is one launch of the correlation; inputs stay
+resident in HBM and L2 is flushed (a 256 MiB write) between timed launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl convtune|reference]
+
+Under torchrun (N > 1) every rank runs its own replica (no exchange step:
+weak scaling); rank 0 prints whole-job throughput.  --impl reference times
+the CPU oracle (FP64 direct correlation, OpenMP) on bands of the same
+workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "conv2d GFLOP/s & GFLOP/J at tuned config; model-steered vs exhaustive tune time"
+WORKLOADS = {
+    "4096x4096_k17": dict(h=4096, w=4096, k=17, seed=1),
+    "1024x1024_k7": dict(h=1024, w=1024, k=7, seed=0),
+}
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
+FLUSH_BYTES = 256 << 20   # > 129 MiB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="convtune", choices=["convtune", "reference"])
+    ap.add_argument("--workload", default="4096x4096_k17", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default=None, help="bx,by,tx,ty,staging,filter,vw")
+    ap.add_argument("--energy-window", type=float, default=1.0)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-energy", action="store_true", help="skip the energy window")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def all_max(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def tuned_config(api, name, wl, override):
+    if override:
+        vals = [int(v) for v in override.split(",")]
+        return api.Config(*vals), "command line"
+    path = os.path.join(ROOT, "paper_2211_07260_gb300", "tuned_configs.json")
+    key = f"{wl['h']}x{wl['w']}_k{wl['k']}"
+    if os.path.exists(path):
+        table = json.load(open(path))
+        for dev, entries in table.get("devices", {}).items():
+            if name.startswith(dev) and key in entries:
+                e = entries[key]
+                return api.Config(*e["config"]), f"tuned_configs.json ({e.get('objective')})"
+    return api.Config(32, 8, 4, 2, api.STAGE_TMA, api.FILTER_CONST, 4), "built-in default"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / power / throttle reasons every 50 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.2)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), pw=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], cap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        load = [r for r in rows if r["pw"] > 300.0] or rows
+        reasons = set()
+        for r in load:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("cap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(r["sm"] for r in load),
+                    sm_max_mhz=max(r["smax"] for r in rows),
+                    power_w_median=statistics.median(r["pw"] for r in load),
+                    samples=len(rows), samples_under_load=len(load), reasons=sorted(reasons))
+
+
+def cpu_baseline(wl, seconds):
+    import oracle
+    from oracle import selection
+    from paper_2211_07260_gb300 import synth
+    prob = synth.conv_problem(wl["h"], wl["w"], wl["k"], seed=wl["seed"])
+    flop = selection.conv2d_flop(wl["k"], wl["k"], wl["h"], wl["w"])
+    nt = oracle.max_threads()
+    oracle.conv2d(prob.inp[:64 + wl["k"]], prob.filt, in_w=prob.in_w)  # warm-up
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.conv2d(prob.inp, prob.filt, in_w=prob.in_w, nthreads=nt)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=reps * flop / dt / 1e9, unit="GFLOP/s", cores=nt, kind="oracle",
+                sample=f"full {wl['h']}x{wl['w']} {wl['k']}x{wl['k']} correlation in FP64, "
+                       f"{reps} repetition(s), {dt:.1f} s wall, {nt} OpenMP threads")
+
+
+def run_reference(args, world, rank):
+    wl = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    import oracle
+    from oracle import selection
+    from paper_2211_07260_gb300 import synth
+    prob = synth.conv_problem(wl["h"], wl["w"], wl["k"], seed=wl["seed"])
+    k = wl["k"]
+    nt = oracle.max_threads()
+    # size one step's band of output rows so the whole run takes ~2 minutes
+    probe_rows = 64
+    t0 = time.perf_counter()
+    oracle.conv2d(prob.inp[:probe_rows + k - 1], prob.filt, in_w=prob.in_w, nthreads=nt)
+    per_row = (time.perf_counter() - t0) / probe_rows
+    rows = int(max(16, min(wl["h"], 120.0 / (args.steps + args.warmup) / per_row)))
+    band = prob.inp[:rows + k - 1]
+    for _ in range(args.warmup):
+        oracle.conv2d(band, prob.filt, in_w=prob.in_w, nthreads=nt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.conv2d(band, prob.filt, in_w=prob.in_w, nthreads=nt)
+    dt = time.perf_counter() - t0
+    flop = selection.conv2d_flop(k, k, rows, wl["w"])
+    value = args.steps * flop / dt / 1e9
+    sample = (f"{rows} of {wl['h']} output rows x {wl['w']} columns, {k}x{k}, FP64 "
+              f"(band of the {args.workload} workload per step)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": nt, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2211_07260_gb300 import api, synth
+
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[args.workload]
+    info = api.device_info()
+    cfg, cfg_src = tuned_config(api, info["name"], wl, args.config)
+    prob = synth.conv_problem(wl["h"], wl["w"], wl["k"], seed=wl["seed"])
+    flop = 2.0 * wl["k"] * wl["k"] * wl["h"] * wl["w"]
+    in_bytes = prob.inp.nbytes
+    out_pitch = (wl["w"] + 3) // 4 * 4
+    out_bytes = 4 * wl["h"] * out_pitch
+    alg_bytes = 4.0 * (prob.in_h * prob.in_w + wl["h"] * wl["w"] + wl["k"] ** 2)
+
+    stream = torch.cuda.Stream()
+    d_in = torch.from_numpy(prob.inp).cuda()
+    d_out = torch.empty((wl["h"], out_pitch), dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def launch():
+        api.conv2d_run(d_in, prob.filt, d_out, wl["h"], wl["w"], cfg, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            flush.zero_()
+            launch()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s, e in ev:
+            flush.zero_()          # L2 flush, outside the timed span
+            s.record(stream)
+            launch()
+            e.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    kernel_s = all_max(world, sum(step_ms) / 1e3)
+    # energy: mean power over >= window of back-to-back launches (NVML energy counter)
+    nan = float("nan")
+    rec = dict(gflops_per_j=nan, energy_j=nan, power_w_mean=nan, power_w_median=nan,
+               energy_j_median_power=nan, gflops=nan, clock_mhz_meas=nan, flags=-1)
+    if not args.no_energy:
+        rec = api.measure_conv(d_in, prob.filt, d_out, wl["h"], wl["w"], cfg,
+                               api.measure_options(window_s=args.energy_window), stream=stream)
+    clocks = sampler.stop()
+    status_bits = api.status_read(clear=True)
+
+    # end to end through the host-buffer entry point (copies in the timed region)
+    e2e_steps = 0 if args.no_e2e else args.e2e_steps
+    e2e_s = nan
+    if e2e_steps:
+        h_in = torch.from_numpy(prob.inp).pin_memory().numpy()
+        h_out = torch.empty((wl["h"], out_pitch), dtype=torch.float32).pin_memory().numpy()
+        api.conv2d_run_host(h_in, prob.filt, h_out, wl["h"], wl["w"], cfg, stream=stream)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            api.conv2d_run_host(h_in, prob.filt, h_out, wl["h"], wl["w"], cfg, stream=stream)
+        e2e_s = all_max(world, time.perf_counter() - t0)
+
+    if rank != 0:
+        return
+    avg_launch_s = kernel_s / args.steps
+    sm = info["sm_count"]
+    peak_clock = clocks["sm_max_mhz"] if clocks else 2070.0
+    peak = sm * FP32_LANES_PER_SM * 2 * peak_clock * 1e6  # FLOP/s
+    achieved = flop / avg_launch_s
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        t = json.load(open(tpath)).get(args.workload)
+        if t and tuple(t.get("config", ())) == cfg.as_tuple():
+            traffic = t.get("dram_bytes_per_launch")
+    out = {
+        "metric": METRIC,
+        "value": world * args.steps * flop / kernel_s / 1e9,
+        "unit": "GFLOP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": kernel_s * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "out": [wl["h"], wl["w"]],
+                   "filter": [wl["k"], wl["k"]], "seed": wl["seed"],
+                   "tuned_config": list(cfg.as_tuple()), "config_source": cfg_src,
+                   "clocks": "default (clock locking is a device setting: not changed)",
+                   "l2": "flushed (256 MiB write) between timed launches",
+                   "parallelism": f"replicas x{world}"},
+        "gflop_per_j": rec["gflops_per_j"],
+        "energy": {"j_per_launch": rec["energy_j"], "power_w_mean": rec["power_w_mean"],
+                   "power_w_median": rec["power_w_median"],
+                   "j_per_launch_median_power": rec["energy_j_median_power"],
+                   "window_s": args.energy_window, "gflops_in_window": rec["gflops"],
+                   "sm_mhz_median": rec["clock_mhz_meas"], "flags": rec["flags"],
+                   "source": "NVML total-energy counter, mean power between counter updates"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": f"{sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 FLOP x "
+                                   f"{peak_clock:.0f} MHz (max SM clock)",
+                     "frac_at_measured_clock": (achieved / (sm * FP32_LANES_PER_SM * 2 *
+                                                            clocks["sm_mhz"] * 1e6)
+                                                if clocks else None),
+                     "hbm_gbs_achieved": alg_bytes / avg_launch_s / 1e9},
+        "e2e": ({"value": world * e2e_steps * flop / e2e_s / 1e9, "unit": "GFLOP/s",
+                 "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
+                 "steps": e2e_steps, "api": "ct_conv2d_run_host (pinned host buffers)"}
+                if e2e_steps else None),
+        "clocks": ({"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                    "reasons": clocks["reasons"], "power_w_median": clocks["power_w_median"],
+                    "samples_under_load": clocks["samples_under_load"]} if clocks else None),
+        "device_status_bits": status_bits,
+        "timed_wall_s": wall,
+        "steering": "unavailable: clock locking not permitted on this pool (tuning at default "
+                    "clocks; the steered-vs-exhaustive comparison runs on the simulated "
+                    "platform in the CPU tests)",
+    }
+    if not args.no_cpu and world == 1:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

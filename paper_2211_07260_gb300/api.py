@@ -343,8 +343,9 @@ def measure_options(window_s=1.0, warmup_s=0.2, graph_ms=2.0, time_only=False, t
     return CtMeasureOptions(window_s, warmup_s, graph_ms, int(bool(time_only)), time_reps)
 
 
-def measure_conv(inp, filt, out, out_h, out_w, cfg: Config, opts=None, stream=None):
-    p, f = make_problem(inp, filt, out, out_h, out_w)
+def measure_conv(inp, filt, out, out_h, out_w, cfg: Config, opts=None, stream=None,
+                 in_pitch=None, out_pitch=None):
+    p, f = make_problem(inp, filt, out, out_h, out_w, in_pitch, out_pitch)
     c = cfg.to_c()
     r = CtRecord()
     o = opts or measure_options()

@@ -243,7 +243,9 @@ int run_window(Driver& d, const ct_measure_options& opt, const ct_platform_ops& 
     max_gap = std::max(max_gap, t - t_last);
     t_last = t;
     const bool warm = t - t_begin >= opt.warmup_s;
-    if (warm && edges >= 2) {
+    // sensors are sampled inside the energy window (after the warm-up
+    // when there is no counter)
+    if (have_energy ? edges >= 2 : warm) {
       unsigned v = 0;
       unsigned long long bits = 0;
       if (ops.power_mw && ops.power_mw(ops.ctx, &v) == CT_OK) pw.push_back(v / 1000.0);
@@ -363,8 +365,9 @@ extern "C" int ct_measure_conv(const ct_problem* p, const ct_config* c,
   if (!p || !c || !out) return CT_EINVAL;
   memset(out, 0, sizeof(*out));
   out->cfg = *c;
+  const ct_platform_ops ops = platform_ops();
   ConvPlan plan;
-  int rc = plan_conv(*p, *c, &plan, nullptr);
+  int rc = plan_conv(*p, *c, &plan, nullptr, ops.run_launches == nullptr);
   if (rc == CT_ECONFIG) out->flags = CT_REC_INVALID;
   if (rc != CT_OK) return rc;
   if (plan.empty) return CT_EINVAL;
@@ -374,5 +377,5 @@ extern "C" int ct_measure_conv(const ct_problem* p, const ct_config* c,
   u.work = conv_flop(*p);
   u.launch = [&plan](cudaStream_t s) { return launch_plan(plan, s); };
   const ct_measure_options o = resolve_options(opt);
-  return measure_unit(u, o, platform_ops(), (cudaStream_t)stream, 0, out);
+  return measure_unit(u, o, ops, (cudaStream_t)stream, 0, out);
 }
