@@ -392,6 +392,73 @@ int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
                     int* range_out, int range_cap, ct_record* records, int cap, int* n_records,
                     int* best_index);
 
+
+/* ---- persistent batched correlation ------------------------------------- */
+
+/*
+ * Many correlations of uneven sizes and odd filter sides (1..17) in one
+ * persistent launch.  A plan copies the taps and an image table to the
+ * device (library scratch, freed by ct_batch_destroy), sorts the images by
+ * (filter side, size class) and captures [work-counter reset + persistent
+ * kernel] into a CUDA graph; ct_batch_run replays it (one host call and one
+ * graph launch per batch).  CTAs of 256 threads, resident-occupancy x SM
+ * count of them, take output tiles from a global atomic counter; each tile
+ * uses the tap order of the plain kernel, so outputs are bitwise identical
+ * to ct_conv2d_run.  Tiles are 4 outputs wide per thread; per bucket
+ * (size class: output area < or >= 512^2; filter side) the block width and
+ * tile height come from ct_batch_tiles (0 entries: 32 x 8 threads, tile_y
+ * 2).
+ */
+typedef struct {
+  const float* in;    /* device, padded input: out_h+k-1 rows of in_pitch   */
+  long in_pitch;
+  const float* filt;  /* HOST, k*k taps row-major (copied at plan time)     */
+  int k;              /* odd, 1..17                                         */
+  float* out;         /* device                                             */
+  long out_pitch;
+  int out_h, out_w;   /* 0 x anything: skipped                              */
+} ct_batch_item;
+
+typedef struct {
+  int block_x[2][18]; /* [size class][k]: 16, 32, 64 or 128 (block_y = 256/block_x) */
+  int tile_y[2][18];  /* [size class][k]: 1, 2 or 4                         */
+} ct_batch_tiles;
+
+typedef struct {
+  int n_images;       /* non-empty images                                   */
+  long long n_items;  /* output tiles                                       */
+  int grid;           /* persistent CTAs                                    */
+  long smem_bytes;    /* dynamic shared memory per CTA                      */
+  double flop;        /* useful FLOP per batch                              */
+  double bytes;       /* algorithmic bytes per batch (inputs, outputs, taps) */
+} ct_batch_stats;
+
+typedef struct ct_batch ct_batch;  /* opaque plan */
+
+int ct_batch_create(const ct_batch_item* items, int n, const ct_batch_tiles* tiles_or_null,
+                    ct_batch** out);
+/* Replay the captured batch on `stream` (asynchronous). */
+int ct_batch_run(ct_batch* b, void* stream);
+/* The comparison: one ct_conv2d_run per image (bucket configuration, taps
+   from the parameter space), in table order, on `stream`. */
+int ct_batch_run_plain(ct_batch* b, void* stream);
+int ct_batch_info(const ct_batch* b, ct_batch_stats* out);
+/* Waits for nothing; the caller must have synchronised work using b. */
+int ct_batch_destroy(ct_batch* b);
+/* Measure the batch (plain = 0: graph replays of the persistent launch;
+   plain = 1: host-issued plain launches, no graph), as ct_measure_conv. */
+int ct_measure_batch(ct_batch* b, int plain, const ct_measure_options* opt, void* stream,
+                     ct_record* out);
+/*
+ * Per-bucket tile tuning: for every (size class, filter side) present, the
+ * median-area image is measured alone as a one-image batch for block_x in
+ * {16, 32, 64, 128} x tile_y in {1, 2, 4} and the objective's best is kept.
+ * records (optional, 12 per bucket) receive the measurements.
+ */
+int ct_batch_tune(const ct_batch_item* items, int n, int objective,
+                  const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,
+                  ct_record* records, int cap, int* n_records);
+
 #ifdef __cplusplus
 }
 #endif

@@ -177,6 +177,14 @@ _SIGS = {
     "ct_measure_power_samples": (c_int, [c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p, c_void_p]),
     "ct_microbench_release": (c_int, []),
+    "ct_batch_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "ct_batch_run": (c_int, [c_void_p, c_void_p]),
+    "ct_batch_run_plain": (c_int, [c_void_p, c_void_p]),
+    "ct_batch_info": (c_int, [c_void_p, c_void_p]),
+    "ct_batch_destroy": (c_int, [c_void_p]),
+    "ct_measure_batch": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "ct_batch_tune": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_int, c_void_p]),
     "ct_tune_steered": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                 c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                 c_void_p, c_int, c_void_p, c_void_p]),
@@ -515,3 +523,108 @@ def tune_steered(inp, filt, out, out_h, out_w, fit_clocks, cfgs=None, supported=
                   fit_wall_s=res.fit_wall_s, tune_wall_s=res.tune_wall_s)
     return result, [int(x) for x in rng[:res.n_range]], \
         [recs[i].to_dict() for i in range(n.value)], best.value
+
+
+# ---- persistent batched correlation ----------------------------------------
+class CtBatchItem(ctypes.Structure):
+    _fields_ = [("in_", c_void_p), ("in_pitch", c_long), ("filt", c_void_p), ("k", c_int),
+                ("out", c_void_p), ("out_pitch", c_long), ("out_h", c_int), ("out_w", c_int)]
+
+
+class CtBatchTiles(ctypes.Structure):
+    _fields_ = [("block_x", (c_int * 18) * 2), ("tile_y", (c_int * 18) * 2)]
+
+    def to_dict(self) -> dict:
+        out = {}
+        for cls in (0, 1):
+            for k in range(18):
+                if self.block_x[cls][k]:
+                    out[(cls, k)] = (self.block_x[cls][k], self.tile_y[cls][k])
+        return out
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "CtBatchTiles":
+        t = cls()
+        for (c, k), (bx, ty) in d.items():
+            t.block_x[c][k] = bx
+            t.tile_y[c][k] = ty
+        return t
+
+
+class CtBatchStats(ctypes.Structure):
+    _fields_ = [("n_images", c_int), ("n_items", ctypes.c_longlong), ("grid", c_int),
+                ("smem_bytes", c_long), ("flop", c_double), ("bytes", c_double)]
+
+
+def batch_items(entries):
+    """CtBatchItem array from (d_in, taps (host 2-D), d_out, out_h, out_w)
+    tuples; returns (array, kept taps)."""
+    arr = (CtBatchItem * len(entries))()
+    keep = []
+    for i, (d_in, filt, d_out, oh, ow) in enumerate(entries):
+        f = _taps(filt)
+        keep.append(f)
+        arr[i] = CtBatchItem(_ptr(d_in), int(d_in.stride(0)) if hasattr(d_in, "stride") else 0,
+                             f.ctypes.data, f.shape[0], _ptr(d_out),
+                             int(d_out.stride(0)) if hasattr(d_out, "stride") else 0,
+                             int(oh), int(ow))
+    return arr, keep
+
+
+class Batch:
+    """A persistent batched plan (ct_batch_create); destroy() or use as a
+    context manager."""
+
+    def __init__(self, entries, tiles: dict | None = None):
+        self._items, self._keep = batch_items(entries)
+        self._h = c_void_p(0)
+        t = CtBatchTiles.from_dict(tiles) if tiles else None
+        _check(lib().ct_batch_create(self._items, len(entries),
+                                     ctypes.byref(t) if t is not None else None,
+                                     ctypes.byref(self._h)), "ct_batch_create")
+
+    def run(self, stream=None):
+        _check(lib().ct_batch_run(self._h, c_void_p(stream_handle(stream))), "ct_batch_run")
+
+    def run_plain(self, stream=None):
+        _check(lib().ct_batch_run_plain(self._h, c_void_p(stream_handle(stream))),
+               "ct_batch_run_plain")
+
+    def info(self) -> dict:
+        st = CtBatchStats()
+        _check(lib().ct_batch_info(self._h, ctypes.byref(st)), "ct_batch_info")
+        return {k: getattr(st, k) for k, _ in CtBatchStats._fields_}
+
+    def measure(self, plain=False, opts=None, stream=None) -> dict:
+        r = CtRecord()
+        o = opts or measure_options()
+        _check(lib().ct_measure_batch(self._h, int(bool(plain)), ctypes.byref(o),
+                                      c_void_p(stream_handle(stream)), ctypes.byref(r)),
+               "ct_measure_batch")
+        return r.to_dict()
+
+    def destroy(self):
+        if self._h:
+            lib().ct_batch_destroy(self._h)
+            self._h = c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+def batch_tune(entries, objective="energy", opts=None, stream=None):
+    """Per-bucket tiles by the tuner (ct_batch_tune): (tiles dict, records)."""
+    items, keep = batch_items(entries)
+    t = CtBatchTiles()
+    cap = 12 * 2 * 18
+    recs = (CtRecord * cap)()
+    n = c_int(0)
+    obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
+    o = opts or measure_options()
+    _check(lib().ct_batch_tune(items, len(entries), obj, ctypes.byref(o),
+                               c_void_p(stream_handle(stream)), ctypes.byref(t), recs, cap,
+                               ctypes.byref(n)), "ct_batch_tune")
+    return t.to_dict(), [recs[i].to_dict() for i in range(n.value)]

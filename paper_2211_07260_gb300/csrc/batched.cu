@@ -1,0 +1,440 @@
+// Persistent, CUDA-graph-captured batched correlation (many images of
+// uneven sizes and odd filter sides in one launch), its per-bucket tile
+// tuning with the energy objective, and the plain one-launch-per-image
+// comparison.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "batched.cuh"
+#include "measure.h"
+#include "platform.h"
+#include "runtime.h"
+
+namespace convtune {
+
+__global__ void __launch_bounds__(kBatchThreads) batched_conv_kernel(const BatchArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  __shared__ long long s_item;
+  __shared__ int s_img;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long w = (long long)atomicAdd(a.counter, 1u);
+      int img = -1;
+      if (w < a.n_items) {
+        // last image whose first item is <= w
+        int lo = 0, hi = a.n_images - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (a.images[mid].first_item <= w) lo = mid;
+          else hi = mid - 1;
+        }
+        img = lo;
+      }
+      s_item = w;
+      s_img = img;
+    }
+    __syncthreads();
+    const long long w = s_item;
+    const int img = s_img;
+    __syncthreads();  // s_item / s_img are rewritten only after this point
+    if (w >= a.n_items) break;
+    const BatchImage& im = a.images[img];
+    const long long t = w - im.first_item;
+    if (t < 0 || t >= (long long)im.tiles_x * im.tiles_y) {
+      if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
+      continue;
+    }
+#define CT_BATCH_CASE(KK)                                   \
+  case KK:                                                  \
+    if (im.ty == 1) batch_tile<KK, 1>(im, t, smem);         \
+    else if (im.ty == 2) batch_tile<KK, 2>(im, t, smem);    \
+    else batch_tile<KK, 4>(im, t, smem);                    \
+    break;
+    switch (im.k) {
+      CT_BATCH_CASE(1)
+      CT_BATCH_CASE(3)
+      CT_BATCH_CASE(5)
+      CT_BATCH_CASE(7)
+      CT_BATCH_CASE(9)
+      CT_BATCH_CASE(11)
+      CT_BATCH_CASE(13)
+      CT_BATCH_CASE(15)
+      CT_BATCH_CASE(17)
+      default:
+        if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
+        break;
+    }
+#undef CT_BATCH_CASE
+  }
+}
+
+namespace {
+
+inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+size_t batch_smem_bytes(int k, int bx, int ty) {
+  const int kp = round_up(k, 4);
+  const int filt = round_up(k * kp, 32);
+  const int by = kBatchThreads / bx;
+  const int tile_w = round_up(bx * kBatchTileX + k - 1, 4);
+  const int tile_h = by * ty + k - 1;
+  return sizeof(float) * (size_t)(filt + tile_w * tile_h);
+}
+
+bool valid_tile(int bx, int ty) {
+  return (bx == 16 || bx == 32 || bx == 64 || bx == 128) && (ty == 1 || ty == 2 || ty == 4);
+}
+
+int size_class(int h, int w) { return (long long)h * w >= 512LL * 512LL ? 1 : 0; }
+
+}  // namespace
+
+}  // namespace convtune
+
+using namespace convtune;
+
+struct ct_batch {
+  int device = 0;
+  std::vector<BatchImage> host_images;   // sorted by (k, class)
+  std::vector<int> order;                // host image index of each table entry
+  std::vector<ct_batch_item> items;      // caller's items (input order)
+  std::vector<std::vector<float>> taps;  // host taps, input order
+  BatchImage* d_images = nullptr;
+  float* d_filters = nullptr;
+  unsigned* d_counter = nullptr;
+  long long n_items = 0;
+  size_t smem = 0;
+  int grid = 0;
+  double flop = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  ~ct_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (d_images) cudaFree(d_images);
+    if (d_filters) cudaFree(d_filters);
+    if (d_counter) cudaFree(d_counter);
+  }
+};
+
+namespace {
+
+// Enqueue one batched launch: counter reset + persistent kernel.
+int enqueue_batch(ct_batch* b, cudaStream_t s) {
+  if (b->n_items == 0) return CT_OK;
+  int err = CT_OK;
+  unsigned* status = device_status_word(&err);
+  if (!status) return err;
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  BatchArgs a;
+  a.images = b->d_images;
+  a.n_images = (int)b->host_images.size();
+  a.n_items = b->n_items;
+  a.counter = b->d_counter;
+  a.status = status;
+  batched_conv_kernel<<<b->grid, kBatchThreads, b->smem, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+// The plain comparison: one ct_conv2d_run per image, configuration from the
+// image's bucket (taps from the parameter space).
+int enqueue_plain(ct_batch* b, cudaStream_t s) {
+  for (size_t i = 0; i < b->host_images.size(); ++i) {
+    const BatchImage& im = b->host_images[i];
+    const ct_batch_item& it = b->items[b->order[i]];
+    ct_problem p;
+    p.in = it.in;
+    p.in_pitch = it.in_pitch;
+    p.filt = b->taps[b->order[i]].data();
+    p.fh = p.fw = it.k;
+    p.out = it.out;
+    p.out_pitch = it.out_pitch;
+    p.out_h = it.out_h;
+    p.out_w = it.out_w;
+    ct_config c;
+    c.block_x = im.bx;
+    c.block_y = kBatchThreads / im.bx;
+    c.tile_x = kBatchTileX;
+    c.tile_y = im.ty;
+    c.staging = CT_STAGE_SMEM;
+    c.filter_mem = CT_FILTER_CONST;
+    c.vec_width = im.vw;
+    const int rc = ct_conv2d_run(&p, &c, s);
+    if (rc != CT_OK) return rc;
+  }
+  return CT_OK;
+}
+
+int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, ct_batch* b) {
+  b->items.assign(items, items + n);
+  b->taps.resize(n);
+  std::vector<BatchImage> imgs;
+  std::vector<int> order;
+  for (int i = 0; i < n; ++i) {
+    const ct_batch_item& it = items[i];
+    if (!it.filt || it.k < 1 || it.k > kMaxK || (it.k & 1) == 0) return CT_EINVAL;
+    if (it.out_h < 0 || it.out_w < 0) return CT_EINVAL;
+    b->taps[i].assign(it.filt, it.filt + it.k * it.k);
+    if (it.out_h == 0 || it.out_w == 0) continue;
+    if (!it.in || !it.out) return CT_EINVAL;
+    if (it.in_pitch < (long)it.out_w + it.k - 1 || it.out_pitch < it.out_w) return CT_EINVAL;
+    if ((long long)it.out_w + it.k > (1LL << 30) || (long long)it.out_h + it.k > (1LL << 30))
+      return CT_EINVAL;
+    BatchImage im;
+    memset(&im, 0, sizeof(im));
+    im.in = it.in;
+    im.out = it.out;
+    im.in_pitch = it.in_pitch;
+    im.out_pitch = it.out_pitch;
+    im.in_h = it.out_h + it.k - 1;
+    im.in_w = it.out_w + it.k - 1;
+    im.out_h = it.out_h;
+    im.out_w = it.out_w;
+    im.k = it.k;
+    const int cls = size_class(it.out_h, it.out_w);
+    int bx = 32, ty = 2;
+    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k])) {
+      bx = tiles->block_x[cls][it.k];
+      ty = tiles->tile_y[cls][it.k];
+    }
+    im.bx = bx;
+    im.ty = ty;
+    const bool aligned = (uintptr_t)it.in % 16 == 0 && it.in_pitch % 4 == 0 &&
+                         (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
+    im.vw = aligned ? 4 : 1;
+    im.tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
+    im.tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
+    imgs.push_back(im);
+    order.push_back(i);
+    b->flop += 2.0 * it.k * it.k * (double)it.out_h * it.out_w;
+  }
+  // bucket order: filter side, then size class, then input order
+  std::vector<int> idx(imgs.size());
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    const int cx = size_class(imgs[x].out_h, imgs[x].out_w);
+    const int cy = size_class(imgs[y].out_h, imgs[y].out_w);
+    return std::make_pair(imgs[x].k, cx) < std::make_pair(imgs[y].k, cy);
+  });
+  long long first = 0;
+  size_t smem = 0;
+  size_t filt_floats = 0;
+  for (int j : idx) {
+    BatchImage im = imgs[j];
+    im.first_item = first;
+    first += (long long)im.tiles_x * im.tiles_y;
+    smem = std::max(smem, batch_smem_bytes(im.k, im.bx, im.ty));
+    filt_floats += (size_t)im.k * round_up(im.k, 4);
+    b->host_images.push_back(im);
+    b->order.push_back(order[j]);
+  }
+  b->n_items = first;
+  b->smem = std::max<size_t>(smem, 16);
+  // device copies: padded taps, then the table pointing at them
+  cudaError_t e;
+  std::vector<float> padded(std::max<size_t>(filt_floats, 1), 0.0f);
+  size_t off = 0;
+  std::vector<size_t> offs;
+  for (size_t q = 0; q < b->host_images.size(); ++q) {
+    const int k = b->host_images[q].k, kp = round_up(k, 4);
+    const std::vector<float>& t = b->taps[b->order[q]];
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < k; ++i) padded[off + j * kp + i] = t[j * k + i];
+    offs.push_back(off);
+    off += (size_t)k * kp;
+  }
+  if ((e = cudaMalloc(&b->d_filters, sizeof(float) * padded.size())) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMemcpy(b->d_filters, padded.data(), sizeof(float) * padded.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_status(e);
+  for (size_t q = 0; q < b->host_images.size(); ++q) b->host_images[q].filt = b->d_filters + offs[q];
+  const size_t tb = sizeof(BatchImage) * std::max<size_t>(b->host_images.size(), 1);
+  if ((e = cudaMalloc(&b->d_images, tb)) != cudaSuccess) return cuda_status(e);
+  if (!b->host_images.empty() &&
+      (e = cudaMemcpy(b->d_images, b->host_images.data(),
+                      sizeof(BatchImage) * b->host_images.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMalloc(&b->d_counter, 256)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemset(b->d_counter, 0, 256)) != cudaSuccess) return cuda_status(e);
+  // persistent grid: resident CTAs per SM x SMs, capped by the work
+  if (b->smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(batched_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)b->smem);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  int per_sm = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
+                                                         kBatchThreads, b->smem)) != cudaSuccess)
+    return cuda_status(e);
+  if (per_sm < 1) return CT_ECONFIG;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device)) != cudaSuccess)
+    return cuda_status(e);
+  b->grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sms, b->n_items));
+  return CT_OK;
+}
+
+int capture_batch(ct_batch* b) {
+  cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_status(e);
+  if ((e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return cuda_status(e);
+  int rc = enqueue_batch(b, b->capture_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->capture_stream, &g);
+  if (rc != CT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ct_batch_create(const ct_batch_item* items, int n, const ct_batch_tiles* tiles,
+                    ct_batch** out) {
+  if (!out || n < 0 || (n > 0 && !items)) return CT_EINVAL;
+  *out = nullptr;
+  ct_batch* b = new (std::nothrow) ct_batch();
+  if (!b) return CT_ENOMEM;
+  cudaError_t e = cudaGetDevice(&b->device);
+  int rc = e == cudaSuccess ? build_batch(items, n, tiles, b) : cuda_status(e);
+  if (rc == CT_OK) rc = capture_batch(b);
+  if (rc != CT_OK) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return CT_OK;
+}
+
+int ct_batch_run(ct_batch* b, void* stream) {
+  if (!b) return CT_EINVAL;
+  if (b->n_items == 0) return CT_OK;
+  return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+}
+
+int ct_batch_run_plain(ct_batch* b, void* stream) {
+  if (!b) return CT_EINVAL;
+  return enqueue_plain(b, (cudaStream_t)stream);
+}
+
+int ct_batch_info(const ct_batch* b, ct_batch_stats* st) {
+  if (!b || !st) return CT_EINVAL;
+  memset(st, 0, sizeof(*st));
+  st->n_images = (int)b->host_images.size();
+  st->n_items = b->n_items;
+  st->grid = b->grid;
+  st->smem_bytes = (long)b->smem;
+  st->flop = b->flop;
+  for (const BatchImage& im : b->host_images)
+    st->bytes += 4.0 * ((double)im.in_h * im.in_w + (double)im.out_h * im.out_w + im.k * im.k);
+  return CT_OK;
+}
+
+int ct_batch_destroy(ct_batch* b) {
+  if (!b) return CT_OK;
+  cudaStreamSynchronize(b->capture_stream);
+  delete b;
+  return CT_OK;
+}
+
+int ct_measure_batch(ct_batch* b, int plain, const ct_measure_options* opt, void* stream,
+                     ct_record* out) {
+  if (!b || !out) return CT_EINVAL;
+  if (b->n_items == 0) return CT_EINVAL;
+  MeasureUnit u;
+  u.kind = CT_UNIT_CONV;
+  u.work = b->flop;
+  u.eager = plain != 0;
+  if (plain)
+    u.launch = [b](cudaStream_t s) { return enqueue_plain(b, s); };
+  else
+    u.launch = [b](cudaStream_t s) { return enqueue_batch(b, s); };
+  return measure_unit(u, resolve_options(opt), platform_ops(), (cudaStream_t)stream, 0, out);
+}
+
+int ct_batch_tune(const ct_batch_item* items, int n, int objective,
+                  const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,
+                  ct_record* records, int cap, int* n_records) {
+  if (!items || n <= 0 || !tiles || !n_records) return CT_EINVAL;
+  if (objective < CT_OBJ_TIME || objective > CT_OBJ_GFLOPS_PER_W) return CT_EINVAL;
+  memset(tiles, 0, sizeof(*tiles));
+  const ct_measure_options mo = resolve_options(opt);
+  const ct_platform_ops ops = platform_ops();
+  // representative image of each bucket: the median output area
+  std::vector<std::vector<int>> bucket(2 * (kMaxK + 1));
+  for (int i = 0; i < n; ++i) {
+    if (items[i].out_h <= 0 || items[i].out_w <= 0) continue;
+    if (items[i].k < 1 || items[i].k > kMaxK || !(items[i].k & 1)) return CT_EINVAL;
+    bucket[size_class(items[i].out_h, items[i].out_w) * (kMaxK + 1) + items[i].k].push_back(i);
+  }
+  const int bxs[4] = {16, 32, 64, 128}, tys[3] = {1, 2, 4};
+  int written = 0, needed = 0;
+  for (auto& v : bucket) needed += v.empty() ? 0 : 12;
+  *n_records = needed;
+  if (records && cap < needed) return CT_ENOMEM;
+  for (int cls = 0; cls < 2; ++cls) {
+    for (int k = 1; k <= kMaxK; k += 2) {
+      std::vector<int>& v = bucket[cls * (kMaxK + 1) + k];
+      if (v.empty()) continue;
+      std::sort(v.begin(), v.end(), [&](int x, int y) {
+        return (long long)items[x].out_h * items[x].out_w <
+               (long long)items[y].out_h * items[y].out_w;
+      });
+      const ct_batch_item& rep = items[v[v.size() / 2]];
+      std::vector<ct_record> recs;
+      for (int bx : bxs)
+        for (int ty : tys) {
+          ct_batch_tiles t;
+          memset(&t, 0, sizeof(t));
+          t.block_x[cls][k] = bx;
+          t.tile_y[cls][k] = ty;
+          ct_batch* b = nullptr;
+          int rc = ct_batch_create(&rep, 1, &t, &b);
+          if (rc != CT_OK) return rc;
+          MeasureUnit u;
+          u.kind = CT_UNIT_CONV;
+          u.work = b->flop;
+          u.launch = [b](cudaStream_t s) { return enqueue_batch(b, s); };
+          ct_record r;
+          rc = measure_unit(u, mo, ops, (cudaStream_t)stream, 0, &r);
+          ct_batch_destroy(b);
+          if (rc != CT_OK) return rc;
+          r.cfg.block_x = bx;
+          r.cfg.block_y = kBatchThreads / bx;
+          r.cfg.tile_x = kBatchTileX;
+          r.cfg.tile_y = ty;
+          r.cfg.staging = CT_STAGE_SMEM;
+          r.cfg.filter_mem = CT_FILTER_SHARED;
+          r.cfg.vec_width = 4;
+          recs.push_back(r);
+          if (records) records[written] = r;
+          ++written;
+        }
+      int best = 0;
+      ct_select_best(recs.data(), (int)recs.size(), objective, nullptr, 0, &best);
+      if (best < 0) best = 0;
+      tiles->block_x[cls][k] = recs[best].cfg.block_x;
+      tiles->tile_y[cls][k] = recs[best].cfg.tile_y;
+    }
+  }
+  *n_records = written;
+  return CT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Persistent batched correlation: many images of uneven sizes and odd
+// filter sides in one launch.  CTAs (256 threads, persistent: occupancy x
+// SM count) take work items -- one output tile of one image -- from a global
+// atomic counter; the image table is sorted by filter side so that CTAs run
+// the same unrolled body at the same time.  Each tile runs the same tap
+// order as the plain kernel, so batched outputs are bitwise identical to
+// plain launches.
+#pragma once
+
+#include "conv2d_kernels.cuh"
+
+namespace convtune {
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchTileX = 4;
+
+// One image of the batch (device table entry).
+struct alignas(16) BatchImage {
+  const float* in;       // padded input (device)
+  float* out;            // output (device)
+  const float* filt;     // taps, k rows of KP = round_up(k, 4) floats (device)
+  long long in_pitch, out_pitch;
+  long long first_item;  // index of this image's first work item
+  int in_h, in_w, out_h, out_w;
+  int k, bx, ty, vw;     // filter side; block_x (block_y = 256 / block_x); tile_y; load width
+  int tiles_x, tiles_y;
+};
+
+struct BatchArgs {
+  const BatchImage* images;
+  int n_images;
+  long long n_items;
+  unsigned* counter;     // work counter, zero at launch
+  unsigned* status;      // device status word
+};
+
+// Fields stage_tile_cp_async() reads.
+struct BatchStage {
+  const float* in;
+  long long in_pitch;
+  int in_h, in_w, vw, tile_w, tile_h, smem_pitch;
+};
+
+template <int K, int TY>
+__device__ __forceinline__ void batch_tile(const BatchImage& im, long long t, float* smem) {
+  constexpr int TX = kBatchTileX;
+  constexpr int KP = (K + 3) / 4 * 4;
+  constexpr int kFilt = (K * KP + 31) / 32 * 32;
+  const int bx = im.bx, by = kBatchThreads / bx;
+  const int tid = threadIdx.x;
+  const int lx = tid % bx, ly = tid / bx;
+  const int ti = (int)(t % im.tiles_x), tj = (int)(t / im.tiles_x);
+  const int gx0 = ti * bx * TX, gy0 = tj * by * TY;
+  float* sfilt = smem;
+  float* tile = smem + kFilt;
+  BatchStage st;
+  st.in = im.in;
+  st.in_pitch = im.in_pitch;
+  st.in_h = im.in_h;
+  st.in_w = im.in_w;
+  st.vw = im.vw;
+  st.tile_w = (bx * TX + K - 1 + 3) / 4 * 4;
+  st.tile_h = by * TY + K - 1;
+  st.smem_pitch = st.tile_w;
+  for (int q = tid; q < K * KP; q += kBatchThreads) sfilt[q] = im.filt[q];
+  stage_tile_cp_async(st, tile, gx0, gy0);
+  __syncthreads();
+
+  float acc[TY][TX];
+  const float* sbase = tile + (ly * TY) * st.smem_pitch + lx * TX;
+  accumulate_tile<K, TX, TY>(
+      acc,
+      [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
+      [&](int j, int i) -> float { return sfilt[j * KP + i]; });
+  const int x0 = gx0 + lx * TX, y0 = gy0 + ly * TY;
+#pragma unroll
+  for (int r = 0; r < TY; ++r) {
+    const int y = y0 + r;
+    if (y < im.out_h) store_run<TX>(im.out + (long long)y * im.out_pitch, x0, im.out_w, im.vw, acc[r]);
+  }
+  __syncthreads();  // the next item reuses the shared memory
+}
+
+}  // namespace convtune

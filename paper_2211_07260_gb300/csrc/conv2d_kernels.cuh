@@ -291,13 +291,15 @@ __device__ __forceinline__ void accumulate_tile(float (&acc)[TY][TX], FetchRow&&
 // Specialised kernel: square odd filter K x K.
 //   STAGED    = false: DIRECT staging; true: SMEM or TMA (args.staging)
 //   FILT_SMEM = false: taps from the parameter (constant) space
-// Dynamic shared memory: [filter K*K (if FILT_SMEM), padded to 32 floats]
+// Dynamic shared memory: [filter K x KP (if FILT_SMEM), padded to 32 floats]
 //                        [tile tile_h x smem_pitch (if STAGED)] [mbarrier]
 // ----------------------------------------------------------------------------
 template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM>
 __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  constexpr int kFiltFloats = FILT_SMEM ? ((K * K + 31) / 32) * 32 : 0;
+  // tap rows padded to a multiple of 4 floats: 4 taps per broadcast LDS.128
+  constexpr int KP = (K + 3) / 4 * 4;
+  constexpr int kFiltFloats = FILT_SMEM ? ((K * KP + 31) / 32) * 32 : 0;
   float* sfilt = reinterpret_cast<float*>(smem_raw);
   float* tile = reinterpret_cast<float*>(smem_raw) + kFiltFloats;
 
@@ -308,7 +310,10 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
   const int y0 = gy0 + threadIdx.y * TY;
 
   if constexpr (FILT_SMEM) {
-    for (int k = threadIdx.y * bx + threadIdx.x; k < K * K; k += bx * by) sfilt[k] = a.w[k];
+    for (int k = threadIdx.y * bx + threadIdx.x; k < K * KP; k += bx * by) {
+      const int j = k / KP, i = k - j * KP;
+      sfilt[k] = i < K ? a.w[j * K + i] : 0.0f;
+    }
   }
   if constexpr (STAGED) {
     if (a.staging == kStageTma) {
@@ -322,7 +327,7 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
 
   float acc[TY][TX];
   auto tap = [&](int j, int i) -> float {
-    if constexpr (FILT_SMEM) return sfilt[j * K + i];
+    if constexpr (FILT_SMEM) return sfilt[j * KP + i];
     else return a.w[j * K + i];
   };
   if constexpr (STAGED) {

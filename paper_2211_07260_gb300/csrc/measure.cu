@@ -70,6 +70,22 @@ class GraphDriver : public Driver {
     cudaEventElapsedTime(&ms, ev0_, ev1_);
     const double t1 = std::max(1e-4, ms / 3.0);
     per_replay = (int)std::min(4096.0, std::max(1.0, ceil(graph_ms / t1)));
+    if (u.eager) {
+      // host launches each replay: what a caller issuing one launch per call pays
+      eager_ = &u.launch;
+    } else {
+      if ((rc = capture(u)) != CT_OK) return rc;
+    }
+    ring_.resize(ring);
+    for (auto& ev : ring_)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_status(e);
+    return CT_OK;
+  }
+
+  int capture(const MeasureUnit& u) {
+    cudaError_t e;
+    int rc = CT_OK;
     // capture
     if ((e = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_status(e);
@@ -86,16 +102,19 @@ class GraphDriver : public Driver {
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaGraphInstantiate(&exec_, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_status(e);
-    ring_.resize(ring);
-    for (auto& ev : ring_)
-      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
-        return cuda_status(e);
-    return CT_OK;
+    return cuda_status(e);
   }
 
   int replay() override {
-    cudaError_t e = cudaGraphLaunch(exec_, s_);
+    cudaError_t e = cudaSuccess;
+    if (eager_) {
+      for (int i = 0; i < per_replay; ++i) {
+        const int rc = (*eager_)(s_);
+        if (rc != CT_OK) return rc;
+      }
+    } else {
+      e = cudaGraphLaunch(exec_, s_);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ring_[tail_ % ring_.size()], s_);
     if (e != cudaSuccess) return cuda_status(e);
     ++tail_;
@@ -128,6 +147,7 @@ class GraphDriver : public Driver {
  private:
   cudaStream_t s_ = nullptr;
   cudaGraphExec_t exec_ = nullptr;
+  const std::function<int(cudaStream_t)>* eager_ = nullptr;
   cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
   std::vector<cudaEvent_t> ring_;
   long long head_ = 0, tail_ = 0;

@@ -18,6 +18,7 @@ struct MeasureUnit {
   const ct_config* cfg = nullptr;          // for CT_UNIT_CONV
   double work = 0.0;                       // useful FLOP (or bytes) per launch
   std::function<int(cudaStream_t)> launch; // enqueue one launch
+  bool eager = false;                      // replay by calling launch() (no graph)
 };
 
 // Defaults filled in for unset (<= 0) options.

@@ -223,7 +223,7 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
       return fail(CT_ECONFIG, "input pointer / pitch not aligned to the load width");
     if (sw > 1 && ((uintptr_t)p.out % (4 * sw) != 0 || p.out_pitch % sw != 0))
       return fail(CT_ECONFIG, "output pointer / pitch not aligned to the store width");
-    size_t smem = L.filt_smem ? sizeof(float) * round_up(K * K, 32) : 0;
+    size_t smem = L.filt_smem ? sizeof(float) * round_up(K * round_up(K, 4), 32) : 0;
     if (staged) {
       L.tile_w = round_up(c.block_x * c.tile_x + K - 1, 4);
       L.tile_h = c.block_y * c.tile_y + K - 1;

@@ -1,0 +1,102 @@
+"""Command-line tuner: run the library's exhaustive search on a seeded
+workload at default clocks and record the chosen configuration.
+
+  python -m paper_2211_07260_gb300.tune --workload 1024x1024_k7 --space basic \\
+      --objective energy --window 0.3 --out tuned_configs.json
+
+--prefilter N first times every point (time objective, no energy window),
+then measures energy only for the N fastest points; without it every point
+gets an energy window.  Results are cached (JSON lines) so a sweep resumes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+from . import api, synth
+
+WORKLOADS = {
+    "1024x1024_k7": (1024, 1024, 7, 0),
+    "4096x4096_k17": (4096, 4096, 17, 1),
+}
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def run(workload, space="basic", objective="energy", window=0.3, prefilter=0, cache=None,
+        out=None, log=print):
+    import torch
+    h, w, k, seed = WORKLOADS[workload]
+    prob = synth.conv_problem(h, w, k, seed=seed)
+    d_in = torch.from_numpy(prob.inp).cuda()
+    d_out = torch.empty((h, (w + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+    cfgs = api.space(api.CT_SPACE_FULL if space == "full" else api.CT_SPACE_BASIC)
+    t0 = time.time()
+    summary = dict(workload=workload, space=space, n_space=len(cfgs), objective=objective,
+                   window_s=window, prefilter=prefilter)
+    if prefilter:
+        recs, best = api.tune(d_in, prob.filt, d_out, h, w, cfgs, None,
+                              api.tune_options("time", window_s=window, warmup_s=0.02,
+                                               time_only=True, cache_path=cache))
+        valid = [r for r in recs if not r["flags"] & api.REC_INVALID]
+        summary["n_valid"] = len(valid)
+        summary["time_pass_wall_s"] = time.time() - t0
+        valid.sort(key=lambda r: r["t_s"])
+        cfgs = [api.Config(*r["cfg"]) for r in valid[:prefilter]]
+        summary["time_best"] = dict(cfg=valid[0]["cfg"], t_s=valid[0]["t_s"],
+                                    gflops=valid[0]["gflops"])
+    recs, best = api.tune(d_in, prob.filt, d_out, h, w, cfgs, None,
+                          api.tune_options(objective, window_s=window, warmup_s=0.1,
+                                           cache_path=cache))
+    valid = [r for r in recs if not r["flags"] & api.REC_INVALID]
+    summary.setdefault("n_valid", len(valid))
+    summary["wall_s"] = time.time() - t0
+    b = recs[best]
+    summary["best"] = dict(cfg=b["cfg"], t_s=b["t_s"], energy_j=b["energy_j"],
+                           gflops=b["gflops"], gflops_per_j=b["gflops_per_j"],
+                           power_w_mean=b["power_w_mean"], sm_mhz=b["clock_mhz_meas"],
+                           flags=b["flags"])
+    tb = api.select_best(recs, "time")
+    eb = api.select_best(recs, "energy")
+    summary["best_time"] = dict(cfg=recs[tb]["cfg"], t_s=recs[tb]["t_s"],
+                                energy_j=recs[tb]["energy_j"])
+    summary["best_energy"] = dict(cfg=recs[eb]["cfg"], t_s=recs[eb]["t_s"],
+                                  energy_j=recs[eb]["energy_j"])
+    summary["same_choice_time_vs_energy"] = recs[tb]["cfg"] == recs[eb]["cfg"]
+    log(json.dumps(summary))
+    if out:
+        table = json.load(open(out)) if os.path.exists(out) else {"devices": {}}
+        name = api.device_info()["name"]
+        table.setdefault("devices", {}).setdefault(name, {})[workload] = dict(
+            config=list(b["cfg"]), objective=objective, space=space, window_s=window,
+            prefilter=prefilter, gflops=b["gflops"], gflops_per_j=b["gflops_per_j"],
+            clocks="default")
+        with open(out, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+            f.write("\n")
+    return summary, recs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="1024x1024_k7", choices=sorted(WORKLOADS))
+    ap.add_argument("--space", default="basic", choices=["basic", "full"])
+    ap.add_argument("--objective", default="energy", choices=sorted(api.OBJECTIVES))
+    ap.add_argument("--window", type=float, default=0.3)
+    ap.add_argument("--prefilter", type=int, default=0)
+    ap.add_argument("--cache", default=None)
+    ap.add_argument("--out", default=os.path.join(HERE, "tuned_configs.json"))
+    ap.add_argument("--records", default=None, help="write every record (JSON lines)")
+    a = ap.parse_args()
+    summary, recs = run(a.workload, a.space, a.objective, a.window, a.prefilter, a.cache, a.out)
+    if a.records:
+        with open(a.records, "w") as f:
+            for r in recs:
+                f.write(json.dumps({k: (None if isinstance(v, float) and math.isnan(v) else v)
+                                    for k, v in r.items()}) + "\n")
+
+
+if __name__ == "__main__":
+    main()

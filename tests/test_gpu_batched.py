@@ -1,0 +1,109 @@
+"""Persistent batched correlation: bitwise equal to plain launches, oracle
+parity on the 256-image workload, per-bucket tuning (GPU)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import MAX_REL, max_rel_err, oracle_ref
+from paper_2211_07260_gb300 import api, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def device_entries(probs, guard=-7.0, pitch_align=4):
+    ents, outs = [], []
+    for p in probs:
+        d_in = torch.from_numpy(p.inp).cuda()
+        pitch = (p.out_w + pitch_align - 1) // pitch_align * pitch_align
+        out = torch.full((p.out_h, pitch), guard, dtype=torch.float32, device="cuda")
+        ents.append((d_in, p.filt, out, p.out_h, p.out_w))
+        outs.append(out)
+    return ents, outs
+
+
+def mixed_problems(n=40, seed=5):
+    probs = synth.batch_problems(n, seed, lo=17, hi=300)
+    # a non-multiple-of-4 pitch (scalar path) and a 1x1 filter
+    probs.append(synth.conv_problem(33, 45, 9, seed=[seed, 99], pitch_align=1))
+    probs.append(synth.conv_problem(70, 64, 1, seed=[seed, 98]))
+    return probs
+
+
+@pytest.mark.parametrize("tiles", [None, "varied"])
+def test_batched_equals_plain_bitwise_and_oracle(tiles):
+    probs = mixed_problems()
+    t = None
+    if tiles == "varied":
+        t = {}
+        for i, k in enumerate(range(1, 18, 2)):
+            t[(0, k)] = ((16, 32, 64, 128)[i % 4], (1, 2, 4)[i % 3])
+            t[(1, k)] = ((128, 64, 32, 16)[i % 4], (4, 1, 2)[i % 3])
+    ents, outs = device_entries(probs)
+    ents_p, outs_p = device_entries(probs)
+    with api.Batch(ents, t) as b, api.Batch(ents_p, t) as bp:
+        st = b.info()
+        assert st["n_images"] == len(probs) and st["n_items"] > st["grid"] > 0
+        b.run()
+        bp.run_plain()
+        torch.cuda.synchronize()
+        for p, o, op in zip(probs, outs, outs_p):
+            a = o.cpu().numpy()
+            c = op.cpu().numpy()
+            assert np.all(a[:, p.out_w:] == -7.0)            # pitch guard untouched
+            assert np.array_equal(a[:, :p.out_w], c[:, :p.out_w])
+            assert max_rel_err(a[:, :p.out_w], oracle_ref(p)) <= MAX_REL
+        # a second replay gives the same bits
+        b.run()
+        torch.cuda.synchronize()
+        for p, o, op in zip(probs, outs, outs_p):
+            assert np.array_equal(o.cpu().numpy()[:, :p.out_w], op.cpu().numpy()[:, :p.out_w])
+    assert api.status_read(clear=True) == 0
+
+
+def test_empty_images_and_errors():
+    p = synth.conv_problem(20, 20, 5, seed=1)
+    d_in = torch.from_numpy(p.inp).cuda()
+    out = torch.zeros((20, 20), dtype=torch.float32, device="cuda")
+    with api.Batch([(d_in, p.filt, out, 0, 20), (d_in, p.filt, out, 20, 20)]) as b:
+        assert b.info()["n_images"] == 1
+        b.run()
+    torch.cuda.synchronize()
+    assert max_rel_err(out.cpu().numpy(), oracle_ref(p)) <= MAX_REL
+    with pytest.raises(api.ConvTuneError):
+        api.Batch([(d_in, np.ones((4, 4), np.float32), out, 20, 20)])  # even side
+    with api.Batch([]) as b:
+        b.run()
+
+
+def test_workload_256_images_oracle_parity():
+    probs = synth.batch_problems(256, seed=2)
+    ents, outs = device_entries(probs)
+    with api.Batch(ents) as b:
+        b.run()
+        torch.cuda.synchronize()
+        st = b.info()
+    flop = sum(2 * p.fh * p.fw * p.out_h * p.out_w for p in probs)
+    assert st["flop"] == pytest.approx(flop)
+    worst = 0.0
+    for p, o in zip(probs, outs):
+        worst = max(worst, max_rel_err(o.cpu().numpy()[:, :p.out_w], oracle_ref(p)))
+    assert worst <= MAX_REL
+
+
+def test_bucket_tuning_and_measurement():
+    probs = synth.batch_problems(24, seed=7, lo=64, hi=700)
+    ents, outs = device_entries(probs)
+    tiles, recs = api.batch_tune(ents, "energy", api.measure_options(window_s=0.2, warmup_s=0.05))
+    ks = {(int(p.out_h * p.out_w >= 512 * 512), p.fh) for p in probs}
+    assert set(tiles) == ks
+    assert len(recs) == 12 * len(ks)
+    for (cls, k), (bx, ty) in tiles.items():
+        assert bx in (16, 32, 64, 128) and ty in (1, 2, 4)
+    with api.Batch(ents, tiles) as b:
+        rb = b.measure(False, api.measure_options(window_s=0.2, warmup_s=0.05))
+        rp = b.measure(True, api.measure_options(window_s=0.2, warmup_s=0.05))
+        assert rb["gflops"] > 0 and rp["gflops"] > 0
+        assert rb["energy_j"] > 0 and rp["energy_j"] > 0
+    torch.cuda.synchronize()
+    for p, o in zip(probs, outs):
+        assert max_rel_err(o.cpu().numpy()[:, :p.out_w], oracle_ref(p)) <= MAX_REL
