@@ -53,6 +53,10 @@ const char* ct_strerror(int status);
 /* Library version, e.g. "convtune 0.1 sm_103a". */
 const char* ct_version(void);
 
+/* Name and text of the last CUDA error this thread saw inside the library
+   (empty if none); the string lives until the thread's next library call. */
+const char* ct_last_error(void);
+
 /* ---- the tuned kernel --------------------------------------------------- */
 
 /* Halo staging of the input tile a CTA needs. */

@@ -119,7 +119,13 @@ class CtSteerResult(ctypes.Structure):
 class ConvTuneError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {strerror(status)} ({status})")
+        detail = ""
+        if status == CT_ECUDA:
+            try:
+                detail = " [" + lib().ct_last_error().decode() + "]"
+            except RuntimeError:
+                pass
+        super().__init__(f"{what}: {strerror(status)} ({status}){detail}")
 
 
 @dataclasses.dataclass(frozen=True)
@@ -150,6 +156,7 @@ _lib = None
 _SIGS = {
     "ct_strerror": (ctypes.c_char_p, [c_int]),
     "ct_version": (ctypes.c_char_p, []),
+    "ct_last_error": (ctypes.c_char_p, []),
     "ct_conv2d_check": (c_int, [c_void_p, c_void_p, ctypes.c_char_p, c_int]),
     "ct_conv2d_run": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ct_conv2d_run_host": (c_int, [c_void_p, c_long, c_void_p, c_int, c_int, c_void_p, c_long,

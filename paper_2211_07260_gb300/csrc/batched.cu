@@ -283,6 +283,9 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
 }
 
 int capture_batch(ct_batch* b) {
+  // allocations are not allowed while capturing: make the status word exist
+  int err = CT_OK;
+  if (!device_status_word(&err)) return err;
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_status(e);
   if ((e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal)) !=

@@ -107,8 +107,14 @@ inline bool one_of_124(int v) { return v == 1 || v == 2 || v == 4; }
 
 }  // namespace
 
+namespace {
+thread_local char g_last_error[256] = "";
+}
+
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return CT_OK;
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e),
+           cudaGetErrorString(e));
   if (e == cudaErrorInvalidConfiguration || e == cudaErrorLaunchOutOfResources) {
     cudaGetLastError();
     return CT_ECONFIG;
@@ -330,6 +336,8 @@ const char* ct_strerror(int status) {
 }
 
 const char* ct_version(void) { return "convtune 0.1 sm_103a"; }
+
+const char* ct_last_error(void) { return g_last_error; }
 
 int ct_conv2d_check(const ct_problem* p, const ct_config* c, char* why, int why_cap) {
   if (!p || !c) return CT_EINVAL;
