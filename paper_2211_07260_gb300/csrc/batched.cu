@@ -267,8 +267,18 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
   if ((e = cudaMemset(b->d_counter, 0, 256)) != cudaSuccess) return cuda_status(e);
   // persistent grid: resident CTAs per SM x SMs, capped by the work
   if (b->smem > 48 * 1024) {
+    // the cap is per kernel and shared by every plan: raise it to the device
+    // limit (a per-plan value could undercut another live plan's graph)
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                    b->device)) != cudaSuccess)
+      return cuda_status(e);
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, batched_conv_kernel)) != cudaSuccess)
+      return cuda_status(e);
+    if (b->smem + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
     e = cudaFuncSetAttribute(batched_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)b->smem);
+                             optin - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return cuda_status(e);
   }
   int per_sm = 0, sms = 0;

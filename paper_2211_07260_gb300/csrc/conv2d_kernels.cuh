@@ -13,9 +13,11 @@
 //   staging           DIRECT: each thread reads its rows straight from global
 //                     memory (vector loads through L1), the horizontal halo of
 //                     a row comes from neighbouring lanes by warp shuffles;
-//                     SMEM: the CTA's halo tile is copied to shared memory with
-//                     cp.async; TMA: the same tile arrives by one 2-D
-//                     cp.async.bulk.tensor copy completing on an mbarrier
+//                     one tile per CTA.
+//                     SMEM / TMA: persistent CTAs, each tile's halo copied to
+//                     one of two shared-memory buffers with cp.async (SMEM) or
+//                     one 2-D cp.async.bulk.tensor completing on an mbarrier
+//                     (TMA), the next tile's copy in flight during compute
 //   filter memory     CONST: taps are read from the kernel's parameter space
 //                     (constant bank, an immediate FFMA operand once the tap
 //                     loops are unrolled); SHARED: taps are copied to shared
@@ -46,6 +48,9 @@ struct alignas(64) ConvArgs {
   int staging;               // kStageDirect / kStageSmem / kStageTma
   int smem_pitch;            // floats per shared-memory tile row
   int tile_w, tile_h;        // staged tile (floats); tile_w % 4 == 0
+  int buf_stride;            // floats between the two staging buffers (% 32 == 0)
+  int tiles_x;               // output tiles per row of tiles (staged variants)
+  long long n_tiles;         // output tiles in total (staged variants)
   float w[NTAPS];            // taps, row-major fh x fw
 };
 
@@ -116,7 +121,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 template <class Args>
-__device__ __forceinline__ void stage_tile_cp_async(const Args& a, float* tile, int gx0, int gy0) {
+__device__ __forceinline__ void issue_tile_cp_async(const Args& a, float* tile, int gx0, int gy0) {
   const int vw = a.vw;
   const int chunks_per_row = a.tile_w / vw;
   const int total = chunks_per_row * a.tile_h;
@@ -130,49 +135,61 @@ __device__ __forceinline__ void stage_tile_cp_async(const Args& a, float* tile, 
     const float* src = avail > 0 ? a.in + (long long)gy * a.in_pitch + gx : a.in;
     cp_async_bytes(tile + r * a.smem_pitch + col, src, vw * 4, avail * 4);
   }
+}
+
+template <class Args>
+__device__ __forceinline__ void stage_tile_cp_async(const Args& a, float* tile, int gx0, int gy0) {
+  issue_tile_cp_async(a, tile, gx0, gy0);
   cp_async_wait_all();
 }
 
-// One 2-D TMA copy of the tile (tile_w <= 256, tile_h <= 256, x % 4 == 0).
-// Returns false in every thread of the CTA if any thread's bounded wait gave
-// up (status bit set).  Ends with a CTA barrier.
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Wait until at most one committed group is still in flight.
+__device__ __forceinline__ void cp_async_wait_one() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// Leader thread: arm the mbarrier for the tile's bytes and start one 2-D TMA
+// copy of the tile (tile_w <= 256, tile_h <= 256, x % 4 == 0).
 template <class Args>
-__device__ __forceinline__ bool stage_tile_tma(const Args& a, float* tile, uint64_t* mbar,
-                                               int gx0, int gy0) {
+__device__ __forceinline__ void issue_tile_tma(const Args& a, float* tile, uint64_t* mbar, int gx0,
+                                               int gy0) {
   const unsigned bar = smem_u32(mbar);
-  const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-  if (leader) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  __syncthreads();
-  if (leader) {
-    const unsigned bytes = static_cast<unsigned>(a.tile_w * a.tile_h * 4);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
-                 "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(tile)),
-        "l"(reinterpret_cast<uint64_t>(&a.tmap)), "r"(gx0), "r"(gy0), "r"(bar)
-        : "memory");
-  }
-  unsigned done = 0;
+  const unsigned bytes = static_cast<unsigned>(a.tile_w * a.tile_h * 4);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(tile)),
+      "l"(reinterpret_cast<uint64_t>(&a.tmap)), "r"(gx0), "r"(gy0), "r"(bar)
+      : "memory");
+}
+
+// Bounded wait for completion of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
+  const unsigned bar = smem_u32(mbar);
   for (unsigned it = 0; it < kMbarSpinLimit; ++it) {
+    unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(0u)
+        : "r"(bar), "r"(parity)
         : "memory");
-    if (done) break;
+    if (done) return true;
   }
-  // every thread takes the same decision, so no thread is left at a barrier
-  if (__syncthreads_or(!done)) {
-    if (leader && a.status) atomicOr(a.status, kStatusTmaTimeout);
-    return false;
-  }
-  return true;
+  return false;
 }
 
 // ----------------------------------------------------------------------------
@@ -301,13 +318,7 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
   constexpr int KP = (K + 3) / 4 * 4;
   constexpr int kFiltFloats = FILT_SMEM ? ((K * KP + 31) / 32) * 32 : 0;
   float* sfilt = reinterpret_cast<float*>(smem_raw);
-  float* tile = reinterpret_cast<float*>(smem_raw) + kFiltFloats;
-
   const int bx = blockDim.x, by = blockDim.y;
-  const int gx0 = blockIdx.x * bx * TX;  // tile origin (input == output coords)
-  const int gy0 = blockIdx.y * by * TY;
-  const int x0 = gx0 + threadIdx.x * TX;
-  const int y0 = gy0 + threadIdx.y * TY;
 
   if constexpr (FILT_SMEM) {
     for (int k = threadIdx.y * bx + threadIdx.x; k < K * KP; k += bx * by) {
@@ -315,29 +326,81 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
       sfilt[k] = i < K ? a.w[j * K + i] : 0.0f;
     }
   }
-  if constexpr (STAGED) {
-    if (a.staging == kStageTma) {
-      uint64_t* mbar = reinterpret_cast<uint64_t*>(tile + a.tile_h * a.smem_pitch);
-      if (!stage_tile_tma(a, tile, mbar, gx0, gy0)) return;
-    } else {
-      stage_tile_cp_async(a, tile, gx0, gy0);
-    }
-  }
-  if constexpr (STAGED || FILT_SMEM) __syncthreads();
-
-  float acc[TY][TX];
   auto tap = [&](int j, int i) -> float {
     if constexpr (FILT_SMEM) return sfilt[j * KP + i];
     else return a.w[j * K + i];
   };
+  float acc[TY][TX];
+
   if constexpr (STAGED) {
-    const float* sbase = tile + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
-    accumulate_tile<K, TX, TY>(
-        acc, [&](int r, float(&rowv)[TX + K - 1]) {
-          fetch_row_smem<K, TX>(rowv, sbase + r * a.smem_pitch);
-        },
-        tap);
+    // Persistent CTAs walk the tiles t = blockIdx.x, blockIdx.x + gridDim.x,
+    // ... with two staging buffers: while tile t is computed from one, the
+    // copy of the next tile is already in flight into the other, and the
+    // freed buffer is refilled with the tile after that.
+    float* const buf0 = sfilt + kFiltFloats;  // buffer b starts at buf0 + b * buf_stride
+    uint64_t* full = reinterpret_cast<uint64_t*>(sfilt + kFiltFloats + 2 * a.buf_stride);
+    const bool tma = a.staging == kStageTma;
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const long long step = gridDim.x;
+    auto issue = [&](long long tt, int b) {
+      const int ti = (int)(tt % a.tiles_x), tj = (int)(tt / a.tiles_x);
+      if (tma) {
+        if (leader)
+          issue_tile_tma(a, buf0 + b * a.buf_stride, &full[b], ti * bx * TX, tj * by * TY);
+      } else {
+        issue_tile_cp_async(a, buf0 + b * a.buf_stride, ti * bx * TX, tj * by * TY);
+      }
+    };
+    if (tma && leader) {
+      mbar_init(&full[0]);
+      mbar_init(&full[1]);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    long long t = blockIdx.x;
+    if (t < a.n_tiles) issue(t, 0);
+    if (!tma) cp_async_commit();
+    if (t + step < a.n_tiles) issue(t + step, 1);
+    if (!tma) cp_async_commit();
+    for (int it = 0; t < a.n_tiles; t += step, ++it) {
+      const int b = it & 1;
+      if (tma) {
+        const bool ok = mbar_wait(&full[b], (unsigned)(it >> 1) & 1u);
+        // every thread takes the same decision, so no thread is left at a barrier
+        if (__syncthreads_or(!ok)) {
+          if (leader && a.status) atomicOr(a.status, kStatusTmaTimeout);
+          return;
+        }
+      } else {
+        cp_async_wait_one();
+        __syncthreads();
+      }
+      const int ti = (int)(t % a.tiles_x), tj = (int)(t / a.tiles_x);
+      const int x0 = ti * bx * TX + threadIdx.x * TX;
+      const int y0 = tj * by * TY + threadIdx.y * TY;
+      const float* sbase =
+          buf0 + b * a.buf_stride + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
+      accumulate_tile<K, TX, TY>(
+          acc, [&](int r, float(&rowv)[TX + K - 1]) {
+            fetch_row_smem<K, TX>(rowv, sbase + r * a.smem_pitch);
+          },
+          tap);
+#pragma unroll
+      for (int r = 0; r < TY; ++r) {
+        const int y = y0 + r;
+        if (y < a.out_h)
+          store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[r]);
+      }
+      __syncthreads();  // buffer b is free
+      if (t + 2 * step < a.n_tiles) issue(t + 2 * step, b);
+      if (!tma) cp_async_commit();
+    }
   } else {
+    if constexpr (FILT_SMEM) __syncthreads();
+    const int gx0 = blockIdx.x * bx * TX;  // tile origin (input == output coords)
+    const int gy0 = blockIdx.y * by * TY;
+    const int x0 = gx0 + threadIdx.x * TX;
+    const int y0 = gy0 + threadIdx.y * TY;
     const int nthr = bx * by;
     const unsigned mask = nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u);
     const int seg = bx < 32 ? bx : 32;  // lanes sharing one contiguous x run
@@ -352,12 +415,11 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
           fetch_row_direct<K, TX>(rowv, row, ok, x0, xs_next, lane, seg, mask, a.in_w, a.vw);
         },
         tap);
-  }
-
 #pragma unroll
-  for (int t = 0; t < TY; ++t) {
-    const int y = y0 + t;
-    if (y < a.out_h) store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[t]);
+    for (int t = 0; t < TY; ++t) {
+      const int y = y0 + t;
+      if (y < a.out_h) store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[t]);
+    }
   }
 }
 

@@ -6,10 +6,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <set>
 #include <string>
+#include <tuple>
 #include <utility>
 
 #include "runtime.h"
@@ -21,7 +23,10 @@ namespace {
 struct DeviceState {
   unsigned* status = nullptr;
   int smem_optin = 0;
-  std::set<std::pair<const void*, size_t>> smem_attr_set;
+  int sm_count = 0;
+  // resident CTAs per SM of (kernel, threads, dynamic shared memory)
+  std::map<std::tuple<const void*, int, size_t>, int> occupancy;
+  std::set<const void*> smem_raised;  // kernels whose dynamic shared-memory cap is raised
   // buffers of the host-buffer entry point
   float* din = nullptr;
   size_t din_bytes = 0;
@@ -50,6 +55,11 @@ DeviceState* current_state(int* dev_out, int* err) {
       return nullptr;
     }
     st.smem_optin = v;
+    e = cudaDeviceGetAttribute(&st.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+      *err = cuda_status(e);
+      return nullptr;
+    }
   }
   if (dev_out) *dev_out = dev;
   *err = CT_OK;
@@ -104,6 +114,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 inline bool one_of_124(int v) { return v == 1 || v == 2 || v == 4; }
+
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in limit
+// once (the attribute is per kernel: setting it per launch size would let a
+// smaller later value break an earlier, larger plan).  Caller holds g_mu.
+cudaError_t raise_smem_cap(DeviceState* st, const void* fn) {
+  if (st->smem_raised.count(fn)) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           st->smem_optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) st->smem_raised.insert(fn);
+  return e;
+}
 
 }  // namespace
 
@@ -233,6 +257,9 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
     if (staged) {
       L.tile_w = round_up(c.block_x * c.tile_x + K - 1, 4);
       L.tile_h = c.block_y * c.tile_y + K - 1;
+      L.tiles_x = (p.out_w + c.block_x * c.tile_x - 1) / (c.block_x * c.tile_x);
+      L.n_tiles = (long long)L.tiles_x *
+                  ((p.out_h + c.block_y * c.tile_y - 1) / (c.block_y * c.tile_y));
       if (c.staging == CT_STAGE_TMA) {
         if (L.tile_w > 256 || L.tile_h > 256)
           return fail(CT_ECONFIG, "TMA box wider or taller than 256 elements");
@@ -246,12 +273,15 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
         if (c.block_x == 16 && c.tile_x == 1)
           while (L.smem_pitch % 32 != 16) L.smem_pitch += 4;
       }
-      smem += sizeof(float) * (size_t)L.tile_h * L.smem_pitch;
-      if (c.staging == CT_STAGE_TMA) smem += 16;  // mbarrier
+      // two staging buffers, each starting on a 128-byte boundary, then two
+      // mbarriers
+      L.buf_stride = round_up(L.tile_h * L.smem_pitch, 32);
+      smem += 2 * sizeof(float) * (size_t)L.buf_stride + 16;
     }
     L.smem_bytes = smem;
   }
-  if (plan->grid.y > 65535u) return fail(CT_ECONFIG, "grid y exceeds 65535");
+  const bool persistent = plan->specialised && L.staging != kStageDirect;
+  if (!persistent && plan->grid.y > 65535u) return fail(CT_ECONFIG, "grid y exceeds 65535");
 
   if (!device_checks) return CT_OK;
   // device-dependent checks
@@ -267,6 +297,31 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
     return fail(CT_ECONFIG, "shared memory exceeds the per-block limit");
   if (c.staging == CT_STAGE_TMA && specialised && !tensor_map_encoder())
     return fail(CT_ENOTSUP, "cuTensorMapEncodeTiled unavailable");
+  if (persistent) {
+    const int threads = c.block_x * c.block_y;
+    int per_sm = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      auto key = std::make_tuple(plan->fn, threads, L.smem_bytes);
+      auto it = st->occupancy.find(key);
+      if (it != st->occupancy.end()) {
+        per_sm = it->second;
+      } else {
+        if (L.smem_bytes > 48 * 1024) {
+          e = raise_smem_cap(st, plan->fn);
+          if (e != cudaSuccess) return fail(cuda_status(e), "cudaFuncSetAttribute failed");
+        }
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan->fn, threads,
+                                                          L.smem_bytes);
+        if (e != cudaSuccess) return fail(cuda_status(e), "occupancy query failed");
+        st->occupancy[key] = per_sm;
+      }
+    }
+    if (per_sm < 1) return fail(CT_ECONFIG, "no CTA of this configuration fits on an SM");
+    const long long resident = (long long)per_sm * st->sm_count;
+    L.grid_x = (int)std::max(1LL, std::min(resident, L.n_tiles));
+    plan->grid = dim3(L.grid_x);
+  }
   return CT_OK;
 }
 
@@ -281,13 +336,8 @@ int launch_plan(ConvPlan& plan, cudaStream_t s) {
   L.status = status;
   if (L.smem_bytes > 48 * 1024) {
     std::lock_guard<std::mutex> lk(g_mu);
-    auto key = std::make_pair(plan.fn, L.smem_bytes);
-    if (!st->smem_attr_set.count(key)) {
-      cudaError_t e = cudaFuncSetAttribute(plan.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)L.smem_bytes);
-      if (e != cudaSuccess) return cuda_status(e);
-      st->smem_attr_set.insert(key);
-    }
+    const cudaError_t e = raise_smem_cap(st, plan.fn);
+    if (e != cudaSuccess) return cuda_status(e);
   }
   L.tmap = nullptr;
   if (plan.specialised && L.staging == kStageTma) {
