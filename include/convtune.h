@@ -463,6 +463,36 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
                   const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,
                   ct_record* records, int cap, int* n_records);
 
+
+/* ---- batched correlation that allocates nothing -------------------------- */
+
+/*
+ * The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory (code running where a framework or memory
+ * pool owns the GPU's memory, or under a rule against cudaMalloc once
+ * serving has started, since an allocation can synchronise the device or
+ * fail under memory pressure).
+ *
+ * It runs the same persistent batched kernel as ct_batch_run on the same
+ * caller-owned inputs and outputs, but every piece of scratch it needs (work
+ * counter, status word, image table, padded taps) lives in one fixed array
+ * compiled into the library (about 373 KB, held on every GPU that loads the
+ * library until the process exits).  Limit: n <= 256 images (filter sides
+ * 1..17, odd); larger n returns CT_EINVAL and ct_last_error() says why.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.  The taps are
+ * copied from `filt` (host) on `stream`; the call returns without
+ * synchronising (inputs must stay alive until the work completes).
+ *
+ * The first call on a device resolves the array's device address and raises
+ * the kernel's shared-memory limit; make that first call before any stream
+ * capture.  Every call reuses the same array (its contents are those of the
+ * last call; the work counter is cleared each call), so calls whose work
+ * overlaps on the GPU -- different streams, or different host threads --
+ * race: serialise them on one stream.
+ */
+int ct_batch_run_noalloc(const ct_batch_item* items, int n, const ct_batch_tiles* tiles_or_null,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

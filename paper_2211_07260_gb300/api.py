@@ -192,6 +192,7 @@ _SIGS = {
     "ct_measure_batch": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ct_batch_tune": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_int, c_void_p]),
+    "ct_batch_run_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "ct_tune_steered": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                 c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                 c_void_p, c_int, c_void_p, c_void_p]),

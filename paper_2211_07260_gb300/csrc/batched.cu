@@ -451,3 +451,170 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched correlation without any device allocation.
+//
+// Some callers cannot allocate device memory: code running where a framework
+// or memory pool owns all of the GPU's memory, or under a policy that forbids
+// cudaMalloc after start-up (allocation can synchronise the device and fail
+// under memory pressure at the worst moment).  For them the batched kernel
+// also runs out of a fixed scratch area compiled into the library: a
+// file-scope device array that every GPU loading the library holds until the
+// process exits.  The caller still owns and passes the inputs and outputs.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxImages = 256;
+constexpr int kNoAllocTapFloats = kMaxK * ((kMaxK + 3) / 4 * 4);  // 17 rows of 20
+constexpr size_t kNoAllocHeaderBytes = 256;  // work counter, status word
+constexpr size_t kNoAllocTableBytes = sizeof(BatchImage) * kNoAllocMaxImages;
+constexpr size_t kNoAllocTapBytes = sizeof(float) * (size_t)kNoAllocTapFloats * kNoAllocMaxImages;
+constexpr size_t kNoAllocBytes = kNoAllocHeaderBytes + kNoAllocTableBytes + kNoAllocTapBytes;
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char* base = nullptr;  // device address of the scratch array
+  int sms = 0;
+};
+
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+// host copy of the image table, per thread (no heap allocation per call)
+thread_local BatchImage t_noalloc_table[kNoAllocMaxImages];
+
+}  // namespace
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// device array: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
+                                    const ct_batch_tiles* tiles, void* stream) {
+  if (n < 0 || (n > 0 && !items)) return CT_EINVAL;
+  if (n > kNoAllocMaxImages) {
+    set_last_error("ct_batch_run_noalloc: more images than the fixed scratch holds (limit 256)");
+    return CT_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= 64) return CT_ENOTSUP;
+  NoAllocDevice nd;
+  {
+    // once per device, with that device current: resolve the array's device
+    // address and lift the kernel's shared-memory cap
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+      void* p = nullptr;
+      if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return cuda_status(e);
+      int optin = 0;
+      if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+          cudaSuccess)
+        return cuda_status(e);
+      cudaFuncAttributes fa;
+      if ((e = cudaFuncGetAttributes(&fa, batched_conv_kernel)) != cudaSuccess)
+        return cuda_status(e);
+      if ((e = cudaFuncSetAttribute(batched_conv_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - (int)fa.sharedSizeBytes)) != cudaSuccess)
+        return cuda_status(e);
+      if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_status(e);
+      d.base = static_cast<unsigned char*>(p);
+      d.ready = true;
+    }
+    nd = d;
+  }
+
+  // validate, and order the images by (filter side, size class)
+  int idx[kNoAllocMaxImages];
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    const ct_batch_item& it = items[i];
+    if (!it.filt || it.k < 1 || it.k > kMaxK || (it.k & 1) == 0) return CT_EINVAL;
+    if (it.out_h < 0 || it.out_w < 0) return CT_EINVAL;
+    if (it.out_h == 0 || it.out_w == 0) continue;
+    if (!it.in || !it.out) return CT_EINVAL;
+    if (it.in_pitch < (long)it.out_w + it.k - 1 || it.out_pitch < it.out_w) return CT_EINVAL;
+    if ((long long)it.out_w + it.k > (1LL << 30) || (long long)it.out_h + it.k > (1LL << 30))
+      return CT_EINVAL;
+    int q = m++;
+    const int key = it.k * 2 + size_class(it.out_h, it.out_w);
+    while (q > 0) {  // stable insertion by key
+      const ct_batch_item& prev = items[idx[q - 1]];
+      if (prev.k * 2 + size_class(prev.out_h, prev.out_w) <= key) break;
+      idx[q] = idx[q - 1];
+      --q;
+    }
+    idx[q] = i;
+  }
+  if (m == 0) return CT_OK;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* counter = reinterpret_cast<unsigned*>(nd.base);
+  unsigned* status = counter + 1;
+  BatchImage* d_table = reinterpret_cast<BatchImage*>(nd.base + kNoAllocHeaderBytes);
+  float* d_taps = reinterpret_cast<float*>(nd.base + kNoAllocHeaderBytes + kNoAllocTableBytes);
+  long long first = 0;
+  size_t smem = 16;
+  for (int q = 0; q < m; ++q) {
+    const ct_batch_item& it = items[idx[q]];
+    BatchImage& im = t_noalloc_table[q];
+    memset(&im, 0, sizeof(im));
+    im.in = it.in;
+    im.out = it.out;
+    im.in_pitch = it.in_pitch;
+    im.out_pitch = it.out_pitch;
+    im.in_h = it.out_h + it.k - 1;
+    im.in_w = it.out_w + it.k - 1;
+    im.out_h = it.out_h;
+    im.out_w = it.out_w;
+    im.k = it.k;
+    const int cls = size_class(it.out_h, it.out_w);
+    int bx = 32, ty = 2;
+    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k])) {
+      bx = tiles->block_x[cls][it.k];
+      ty = tiles->tile_y[cls][it.k];
+    }
+    im.bx = bx;
+    im.ty = ty;
+    const bool aligned = (uintptr_t)it.in % 16 == 0 && it.in_pitch % 4 == 0 &&
+                         (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
+    im.vw = aligned ? 4 : 1;
+    im.tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
+    im.tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
+    im.first_item = first;
+    first += (long long)im.tiles_x * im.tiles_y;
+    smem = std::max(smem, batch_smem_bytes(it.k, bx, ty));
+    // taps: k rows padded to round_up(k, 4) floats (the padding is never used
+    // as a tap), copied straight from the caller's host array
+    const int kp = round_up(it.k, 4);
+    float* dst = d_taps + (size_t)q * kNoAllocTapFloats;
+    im.filt = dst;
+    e = cudaMemcpy2DAsync(dst, sizeof(float) * kp, it.filt, sizeof(float) * it.k,
+                          sizeof(float) * it.k, it.k, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if ((e = cudaMemcpyAsync(d_table, t_noalloc_table, sizeof(BatchImage) * m,
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  // the work counter must start at zero; the status word is cleared too
+  if ((e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), s)) != cudaSuccess)
+    return cuda_status(e);
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
+                                                         kBatchThreads, smem)) != cudaSuccess)
+    return cuda_status(e);
+  if (per_sm < 1) return CT_ECONFIG;
+  BatchArgs a;
+  a.images = d_table;
+  a.n_images = m;
+  a.n_items = first;
+  a.counter = counter;
+  a.status = status;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * nd.sms, first));
+  batched_conv_kernel<<<grid, kBatchThreads, smem, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}

@@ -389,6 +389,14 @@ const char* ct_version(void) { return "convtune 0.1 sm_103a"; }
 
 const char* ct_last_error(void) { return g_last_error; }
 
+}  // extern "C"
+
+namespace convtune {
+void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace convtune
+
+extern "C" {
+
 int ct_conv2d_check(const ct_problem* p, const ct_config* c, char* why, int why_cap) {
   if (!p || !c) return CT_EINVAL;
   ConvPlan plan;

@@ -40,6 +40,9 @@ unsigned* device_status_word(int* err);
 // callers that want detail).
 int cuda_status(cudaError_t e);
 
+// Record a message for ct_last_error() (argument errors worth explaining).
+void set_last_error(const char* msg);
+
 // Useful work of one correlation: 2 * fh * fw * out_h * out_w FLOP.
 double conv_flop(const ct_problem& p);
 // Algorithmic bytes of one correlation: padded input read once, output
