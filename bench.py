@@ -31,6 +31,9 @@ METRIC = "conv2d GFLOP/s & GFLOP/J at tuned config; model-steered vs exhaustive 
 WORKLOADS = {
     "4096x4096_k17": dict(h=4096, w=4096, k=17, seed=1),
     "1024x1024_k7": dict(h=1024, w=1024, k=7, seed=0),
+    # 256 images, sides log-uniform [256, 2048], odd k 3..17 (seed 2): one
+    # persistent CUDA-graph launch vs one plain launch per image
+    "batched256": dict(n=256, seed=2),
 }
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 FLUSH_BYTES = 256 << 20   # > 129 MiB L2
@@ -212,11 +215,73 @@ def run_reference(args, world, rank):
     }))
 
 
+def run_batched(args, world, rank, local):
+    """The batched workload: GFLOP/s and GFLOP/J of the persistent launch and of
+    one plain launch per image, both measured by the library's energy window."""
+    import torch
+
+    from paper_2211_07260_gb300 import api, synth
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[args.workload]
+    probs = synth.batch_problems(wl["n"], wl["seed"])
+    ents = []
+    for p in probs:
+        d_in = torch.from_numpy(p.inp).cuda()
+        out = torch.empty((p.out_h, (p.out_w + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+        ents.append((d_in, p.filt, out, p.out_h, p.out_w))
+    tiles, src = None, "default tiles"
+    path = os.path.join(ROOT, "paper_2211_07260_gb300", "tuned_configs.json")
+    if os.path.exists(path):
+        t = json.load(open(path)).get("batched_tiles", {}).get(api.device_info()["name"])
+        if t:
+            tiles = {tuple(int(x) for x in k.split(",")): tuple(v) for k, v in t.items()}
+            src = "tuned_configs.json (energy objective per bucket)"
+    opts = api.measure_options(window_s=args.energy_window)
+    with api.Batch(ents, tiles) as b:
+        st = b.info()
+        stream = torch.cuda.Stream()
+        for _ in range(max(3, args.warmup)):
+            b.run(stream)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        t_s = all_max(world, e0.elapsed_time(e1) / 1e3)
+        rb = b.measure(False, opts)
+        rp = b.measure(True, opts)
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": world * args.steps * st["flop"] / t_s / 1e9, "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "images": st["n_images"], "tiles": st["n_items"],
+                   "persistent_ctas": st["grid"], "tiles_source": src,
+                   "l2": "inputs 1.5 GB > L2", "parallelism": f"replicas x{world}"},
+        "gflop_per_j": rb["gflops_per_j"],
+        "batched": {"gflops": rb["gflops"], "gflop_per_j": rb["gflops_per_j"],
+                    "power_w_mean": rb["power_w_mean"], "flags": rb["flags"]},
+        "plain_per_image": {"gflops": rp["gflops"], "gflop_per_j": rp["gflops_per_j"],
+                            "power_w_mean": rp["power_w_mean"], "flags": rp["flags"]},
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched256":
+        run_batched(args, world, rank, local)
         return
     import numpy as np
     import torch

@@ -192,6 +192,18 @@ typedef struct {
   int (*run_launches)(void* ctx, int kind, const ct_config* cfg, int n, double* elapsed_ms);
 } ct_platform_ops;
 
+/* One reading of the platform's sensors (the observer record of Section
+   III-B): NaN / 0 for sensors the table does not provide. */
+typedef struct {
+  double energy_j;        /* total-energy counter (since driver load)       */
+  double power_w;         /* power reading (NVML: averaged over ~100 ms)    */
+  double sm_clock_mhz;
+  double temp_c;
+  unsigned long long throttle_reasons;
+  int other_processes;
+} ct_sensors;
+int ct_read_sensors(ct_sensors* out);
+
 /* Install a platform table (copied); NULL restores the NVML table. */
 int ct_set_platform_ops(const ct_platform_ops* ops);
 /* CT_OK if the NVML table found libnvidia-ml and the current device. */
@@ -492,6 +504,59 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
  */
 int ct_batch_run_noalloc(const ct_batch_item* items, int n, const ct_batch_tiles* tiles_or_null,
                          void* stream);
+
+
+/* ---- request server with continuous batching ---------------------------- */
+
+/*
+ * Requests (host input, host taps, host output buffer) are submitted at any
+ * time from any thread.  A worker thread admits them in arrival order while
+ * a device-resident pool (allocated at creation, at most 90 % of the free
+ * device memory) has room for their buffers, and dispatches admitted
+ * requests as batches on up to n_streams streams at once: copy in, one
+ * persistent batched launch (or, with `plain`, one plain launch per
+ * request), copy out.  A batch leaves when it is full, when no batch is in
+ * flight, or when its oldest request has waited max_wait_s; requests that
+ * arrive while others run join the next batch.  Results are bitwise equal to
+ * a request served alone.  Latency = submission to completion seen by the
+ * worker.  Host buffers must stay valid until the request completes.
+ */
+typedef struct {
+  int n_streams;         /* batches in flight at once, 1..64                */
+  int max_batch;         /* requests per batch, 1..4096                     */
+  long long pool_bytes;  /* device pool for request buffers                 */
+  double max_wait_s;     /* batching delay bound                            */
+  int plain;             /* 1: one plain kernel per request (comparison)    */
+  int use_tiles;         /* 1: per-bucket tiles from `tiles`                */
+  ct_batch_tiles tiles;
+} ct_server_options;
+
+typedef struct {
+  long long submitted, completed, rejected;
+  double p50_s, p99_s, mean_s, max_s;  /* request latency                   */
+  double wall_s;         /* creation or last reset to the last completion   */
+  double flop;           /* useful FLOP of completed requests               */
+  double energy_j;       /* energy-counter difference over the same span    */
+  long long batches;
+  double mean_batch;     /* requests per batch                              */
+  long long pool_used_bytes;
+} ct_server_stats;
+
+typedef struct ct_server ct_server;
+
+int ct_server_create(const ct_server_options* opt, ct_server** out);
+/* Queue one request (k odd, 1..17); CT_ENOMEM if it can never fit the pool. */
+int ct_server_submit(ct_server* sv, const float* in_host, long in_pitch, const float* filt, int k,
+                     float* out_host, long out_pitch, int out_h, int out_w, long long* id);
+/* Wait for one request (CT_ETIMEOUT on timeout); returns its status and
+   releases its record.  latency_s may be NULL. */
+int ct_server_wait(ct_server* sv, long long id, double timeout_s, double* latency_s);
+/* Wait for every submitted request; releases their records. */
+int ct_server_drain(ct_server* sv, double timeout_s);
+/* Statistics since creation or the last reset (reset = 1 starts a new span). */
+int ct_server_stats_get(ct_server* sv, int reset, ct_server_stats* out);
+/* Finish every queued request, stop the worker and free the server. */
+int ct_server_destroy(ct_server* sv);
 
 #ifdef __cplusplus
 }

@@ -193,6 +193,14 @@ _SIGS = {
     "ct_batch_tune": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_int, c_void_p]),
     "ct_batch_run_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "ct_server_create": (c_int, [c_void_p, c_void_p]),
+    "ct_server_submit": (c_int, [c_void_p, c_void_p, c_long, c_void_p, c_int, c_void_p, c_long,
+                                 c_int, c_int, c_void_p]),
+    "ct_server_wait": (c_int, [c_void_p, ctypes.c_longlong, c_double, c_void_p]),
+    "ct_server_drain": (c_int, [c_void_p, c_double]),
+    "ct_server_stats_get": (c_int, [c_void_p, c_int, c_void_p]),
+    "ct_server_destroy": (c_int, [c_void_p]),
+    "ct_read_sensors": (c_int, [c_void_p]),
     "ct_tune_steered": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                 c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                 c_void_p, c_int, c_void_p, c_void_p]),
@@ -342,6 +350,18 @@ def set_platform_ops(ops: "CtPlatformOps | None"):
     _check(lib().ct_set_platform_ops(ctypes.byref(ops) if ops is not None else None),
            "ct_set_platform_ops")
     _platform_keepalive = ops
+
+
+class CtSensors(ctypes.Structure):
+    _fields_ = [("energy_j", c_double), ("power_w", c_double), ("sm_clock_mhz", c_double),
+                ("temp_c", c_double), ("throttle_reasons", ctypes.c_ulonglong),
+                ("other_processes", c_int)]
+
+
+def read_sensors() -> dict:
+    s = CtSensors()
+    _check(lib().ct_read_sensors(ctypes.byref(s)), "ct_read_sensors")
+    return {k: getattr(s, k) for k, _ in CtSensors._fields_}
 
 
 def nvml_status() -> int:
@@ -636,3 +656,65 @@ def batch_tune(entries, objective="energy", opts=None, stream=None):
                                c_void_p(stream_handle(stream)), ctypes.byref(t), recs, cap,
                                ctypes.byref(n)), "ct_batch_tune")
     return t.to_dict(), [recs[i].to_dict() for i in range(n.value)]
+
+
+# ---- request server ---------------------------------------------------------
+class CtServerOptions(ctypes.Structure):
+    _fields_ = [("n_streams", c_int), ("max_batch", c_int), ("pool_bytes", ctypes.c_longlong),
+                ("max_wait_s", c_double), ("plain", c_int), ("use_tiles", c_int),
+                ("tiles", CtBatchTiles)]
+
+
+class CtServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("p50_s", c_double), ("p99_s", c_double),
+                ("mean_s", c_double), ("max_s", c_double), ("wall_s", c_double),
+                ("flop", c_double), ("energy_j", c_double), ("batches", ctypes.c_longlong),
+                ("mean_batch", c_double), ("pool_used_bytes", ctypes.c_longlong)]
+
+
+class Server:
+    """Continuous-batching request server (ct_server_*).  Host buffers passed
+    to submit() must stay alive until the request completes."""
+
+    def __init__(self, n_streams=4, max_batch=64, pool_bytes=8 << 30, max_wait_s=200e-6,
+                 plain=False, tiles: dict | None = None):
+        o = CtServerOptions(n_streams, max_batch, pool_bytes, max_wait_s, int(bool(plain)),
+                            1 if tiles else 0, CtBatchTiles.from_dict(tiles) if tiles
+                            else CtBatchTiles())
+        self._h = c_void_p(0)
+        _check(lib().ct_server_create(ctypes.byref(o), ctypes.byref(self._h)), "ct_server_create")
+        self._keep = {}
+
+    def submit(self, inp: np.ndarray, filt, out: np.ndarray, out_h: int, out_w: int) -> int:
+        f = _taps(filt)
+        rid = ctypes.c_longlong(0)
+        _check(lib().ct_server_submit(self._h, inp.ctypes.data, inp.shape[1], f.ctypes.data,
+                                      f.shape[0], out.ctypes.data, out.shape[1], int(out_h),
+                                      int(out_w), ctypes.byref(rid)), "ct_server_submit")
+        return rid.value
+
+    def wait(self, rid: int, timeout_s=60.0) -> float:
+        lat = c_double(0)
+        _check(lib().ct_server_wait(self._h, rid, timeout_s, ctypes.byref(lat)), "ct_server_wait")
+        return lat.value
+
+    def drain(self, timeout_s=120.0):
+        _check(lib().ct_server_drain(self._h, timeout_s), "ct_server_drain")
+
+    def stats(self, reset=False) -> dict:
+        st = CtServerStats()
+        _check(lib().ct_server_stats_get(self._h, int(bool(reset)), ctypes.byref(st)),
+               "ct_server_stats_get")
+        return {k: getattr(st, k) for k, _ in CtServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().ct_server_destroy(self._h)
+            self._h = c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -618,3 +618,70 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   batched_conv_kernel<<<grid, kBatchThreads, smem, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------
+// Helpers for other units of the library (the request server) that build
+// batch tables in their own memory and launch the batched kernel.
+// ---------------------------------------------------------------------------
+namespace convtune {
+
+int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, BatchImage* im,
+                          size_t* smem) {
+  if (!it.filt || it.k < 1 || it.k > kMaxK || (it.k & 1) == 0) return CT_EINVAL;
+  if (it.out_h <= 0 || it.out_w <= 0 || !it.in || !it.out) return CT_EINVAL;
+  if (it.in_pitch < (long)it.out_w + it.k - 1 || it.out_pitch < it.out_w) return CT_EINVAL;
+  memset(im, 0, sizeof(*im));
+  im->in = it.in;
+  im->out = it.out;
+  im->in_pitch = it.in_pitch;
+  im->out_pitch = it.out_pitch;
+  im->in_h = it.out_h + it.k - 1;
+  im->in_w = it.out_w + it.k - 1;
+  im->out_h = it.out_h;
+  im->out_w = it.out_w;
+  im->k = it.k;
+  const int cls = size_class(it.out_h, it.out_w);
+  int bx = 32, ty = 2;
+  if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k])) {
+    bx = tiles->block_x[cls][it.k];
+    ty = tiles->tile_y[cls][it.k];
+  }
+  im->bx = bx;
+  im->ty = ty;
+  const bool aligned = (uintptr_t)it.in % 16 == 0 && it.in_pitch % 4 == 0 &&
+                       (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
+  im->vw = aligned ? 4 : 1;
+  im->tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
+  im->tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
+  *smem = std::max(*smem, batch_smem_bytes(it.k, bx, ty));
+  return CT_OK;
+}
+
+int launch_batched_kernel(const BatchArgs& a, size_t smem, int sms, cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t raised = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    raised = cudaGetDevice(&dev);
+    if (raised == cudaSuccess)
+      raised = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (raised == cudaSuccess) raised = cudaFuncGetAttributes(&fa, batched_conv_kernel);
+    if (raised == cudaSuccess)
+      raised = cudaFuncSetAttribute(batched_conv_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - (int)fa.sharedSizeBytes);
+  });
+  if (raised != cudaSuccess) return cuda_status(raised);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
+                                                                kBatchThreads, smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (per_sm < 1) return CT_ECONFIG;
+  const int grid =
+      (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sms, a.n_items));
+  batched_conv_kernel<<<grid, kBatchThreads, smem, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace convtune

@@ -1,0 +1,115 @@
+"""Serving driver: Poisson-arrival correlation requests through the library's
+continuous-batching server (ct_server_*), and the same arrivals served with
+one plain kernel per request.
+
+  python -m paper_2211_07260_gb300.serve --rates 100,1000,10000 --seconds 10
+
+Request shapes follow the batched workload's law (sides log-uniform in
+[256, 2048], odd filter sides 3..17); a pool of distinct seeded payloads in
+pinned host memory is reused cyclically (the arrival process and the shape
+of each request come from their own seeded streams).  Reports p50/p99
+latency, request throughput, GFLOP/s and joules per request (total and above
+the idle power measured just before).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import api, synth
+
+
+def make_payloads(n, seed=3, lo=256, hi=2048):
+    import torch
+    shapes = synth.request_shapes(n, seed, lo, hi)
+    pay = []
+    for i, sh in enumerate(shapes):
+        p = synth.request_problem(seed, i, sh)
+        inp = torch.from_numpy(p.inp).pin_memory().numpy()
+        out = torch.empty((p.out_h, (p.out_w + 3) // 4 * 4), dtype=torch.float32).pin_memory()
+        pay.append((p, inp, out.numpy()))
+    return pay
+
+
+def idle_power(seconds=1.0):
+    samples = []
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        samples.append(api.read_sensors()["power_w"])
+        time.sleep(0.05)
+    return float(np.median(samples))
+
+
+def serve_rate(payloads, rate, seconds, max_requests, seed=3, plain=False, tiles=None,
+               n_streams=4, max_batch=64, max_wait_s=200e-6, pool_bytes=16 << 30, p_idle=None):
+    n = int(min(max_requests, max(1, rate * seconds)))
+    arrivals = synth.poisson_arrivals(rate, n, seed)
+    with api.Server(n_streams=n_streams, max_batch=max_batch, pool_bytes=pool_bytes,
+                    max_wait_s=max_wait_s, plain=plain, tiles=tiles) as sv:
+        # warm-up (kernels loaded, pool touched), then a fresh statistics span
+        for i in range(min(8, len(payloads))):
+            p, inp, out = payloads[i]
+            sv.submit(inp, p.filt, out, p.out_h, p.out_w)
+        sv.drain()
+        sv.stats(reset=True)
+        t0 = time.perf_counter()
+        for i in range(n):
+            target = t0 + arrivals[i]
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 2e-3:
+                    time.sleep(target - now - 1e-3)
+            p, inp, out = payloads[i % len(payloads)]
+            sv.submit(inp, p.filt, out, p.out_h, p.out_w)
+        submit_lag = time.perf_counter() - (t0 + arrivals[-1])
+        sv.drain(timeout_s=600.0)
+        st = sv.stats()
+    res = dict(rate_hz=rate, mode="plain" if plain else "batched", requests=st["completed"],
+               p50_ms=st["p50_s"] * 1e3, p99_ms=st["p99_s"] * 1e3, max_ms=st["max_s"] * 1e3,
+               req_per_s=st["completed"] / st["wall_s"], gflops=st["flop"] / st["wall_s"] / 1e9,
+               wall_s=st["wall_s"], mean_batch=st["mean_batch"], batches=st["batches"],
+               energy_j=st["energy_j"], j_per_req=st["energy_j"] / max(1, st["completed"]),
+               gflop_per_j=st["flop"] / 1e9 / st["energy_j"] if st["energy_j"] > 0 else None,
+               submit_lag_s=submit_lag)
+    if p_idle is not None:
+        above = st["energy_j"] - p_idle * st["wall_s"]
+        res["p_idle_w"] = p_idle
+        res["j_per_req_above_idle"] = above / max(1, st["completed"])
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--rates", default="100,300,1000,3000,10000,20000")
+    ap.add_argument("--seconds", type=float, default=10.0)
+    ap.add_argument("--max-requests", type=int, default=20000)
+    ap.add_argument("--payloads", type=int, default=256)
+    ap.add_argument("--modes", default="batched,plain")
+    ap.add_argument("--tiles", default=None, help="JSON file of per-bucket tiles")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    tiles = None
+    if a.tiles:
+        raw = json.load(open(a.tiles))
+        tiles = {tuple(int(x) for x in k.split(",")): tuple(v) for k, v in raw.items()}
+    payloads = make_payloads(a.payloads)
+    p_idle = idle_power()
+    rows = []
+    for rate in [float(r) for r in a.rates.split(",")]:
+        for mode in a.modes.split(","):
+            r = serve_rate(payloads, rate, a.seconds, a.max_requests, plain=(mode == "plain"),
+                           tiles=tiles, p_idle=p_idle)
+            print(json.dumps(r), flush=True)
+            rows.append(r)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(rows, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -79,9 +79,36 @@ def run(workload, space="basic", objective="energy", window=0.3, prefilter=0, ca
     return summary, recs
 
 
+def tune_batched(objective="energy", window=0.3, out=None, n=256, seed=2, log=print):
+    """Per-bucket tiles of the batched workload (ct_batch_tune) into the
+    tuned-configuration table."""
+    import torch
+    probs = synth.batch_problems(n, seed)
+    ents = []
+    for p in probs:
+        d_in = torch.from_numpy(p.inp).cuda()
+        o = torch.empty((p.out_h, (p.out_w + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+        ents.append((d_in, p.filt, o, p.out_h, p.out_w))
+    t0 = time.time()
+    tiles, recs = api.batch_tune(ents, objective, api.measure_options(window_s=window,
+                                                                      warmup_s=0.1))
+    log(json.dumps(dict(batched_tiles={f"{c},{k}": v for (c, k), v in tiles.items()},
+                        points=len(recs), wall_s=time.time() - t0)))
+    if out:
+        table = json.load(open(out)) if os.path.exists(out) else {"devices": {}}
+        name = api.device_info()["name"]
+        table.setdefault("batched_tiles", {})[name] = {f"{c},{k}": list(v)
+                                                       for (c, k), v in tiles.items()}
+        with open(out, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+            f.write("\n")
+    return tiles, recs
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="1024x1024_k7", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="1024x1024_k7",
+                    choices=sorted(WORKLOADS) + ["batched256"])
     ap.add_argument("--space", default="basic", choices=["basic", "full"])
     ap.add_argument("--objective", default="energy", choices=sorted(api.OBJECTIVES))
     ap.add_argument("--window", type=float, default=0.3)
@@ -90,6 +117,9 @@ def main():
     ap.add_argument("--out", default=os.path.join(HERE, "tuned_configs.json"))
     ap.add_argument("--records", default=None, help="write every record (JSON lines)")
     a = ap.parse_args()
+    if a.workload == "batched256":
+        tune_batched(a.objective, a.window, a.out)
+        return
     summary, recs = run(a.workload, a.space, a.objective, a.window, a.prefilter, a.cache, a.out)
     if a.records:
         with open(a.records, "w") as f:
