@@ -157,9 +157,12 @@ struct ct_server {
 int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
   cudaError_t e;
   int rc = CT_OK;
-  // inputs in
+  // inputs in: the columns the kernel reads, rows at the caller's pitch
   for (Request* r : batch) {
-    e = cudaMemcpyAsync(pool + r->off, r->in_host, r->in_bytes, cudaMemcpyHostToDevice, sl.s);
+    const size_t pitch = sizeof(float) * (size_t)r->in_pitch;
+    e = cudaMemcpy2DAsync(pool + r->off, pitch, r->in_host, pitch,
+                          sizeof(float) * (size_t)(r->out_w + r->k - 1), r->out_h + r->k - 1,
+                          cudaMemcpyHostToDevice, sl.s);
     if (e != cudaSuccess) return cuda_status(e);
   }
   if (opt.plain) {
@@ -241,11 +244,12 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
     a.status = status;
     if ((rc = launch_batched_kernel(a, smem, sms, sl.s)) != CT_OK) return rc;
   }
-  // outputs back
+  // outputs back: only the out_w computed columns of each row (the caller's
+  // padding columns are left untouched)
   for (Request* r : batch) {
-    const size_t ob = sizeof(float) * (size_t)r->out_h * r->out_pitch;
-    e = cudaMemcpyAsync(r->out_host, pool + r->off + r->in_bytes, ob, cudaMemcpyDeviceToHost,
-                        sl.s);
+    const size_t pitch = sizeof(float) * (size_t)r->out_pitch;
+    e = cudaMemcpy2DAsync(r->out_host, pitch, pool + r->off + r->in_bytes, pitch,
+                          sizeof(float) * (size_t)r->out_w, r->out_h, cudaMemcpyDeviceToHost, sl.s);
     if (e != cudaSuccess) return cuda_status(e);
   }
   if ((e = cudaEventRecord(sl.ev, sl.s)) != cudaSuccess) return cuda_status(e);
