@@ -336,48 +336,62 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
     // Persistent CTAs walk the tiles t = blockIdx.x, blockIdx.x + gridDim.x,
     // ... with two staging buffers: while tile t is computed from one, the
     // copy of the next tile is already in flight into the other, and the
-    // freed buffer is refilled with the tile after that.
+    // freed buffer is refilled with the tile after that.  Tile coordinates
+    // advance by adding the grid stride (no divisions in the loop).
     float* const buf0 = sfilt + kFiltFloats;  // buffer b starts at buf0 + b * buf_stride
     uint64_t* full = reinterpret_cast<uint64_t*>(sfilt + kFiltFloats + 2 * a.buf_stride);
+    __shared__ int s_fail;
     const bool tma = a.staging == kStageTma;
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-    const long long step = gridDim.x;
-    auto issue = [&](long long tt, int b) {
-      const int ti = (int)(tt % a.tiles_x), tj = (int)(tt / a.tiles_x);
-      if (tma) {
-        if (leader)
-          issue_tile_tma(a, buf0 + b * a.buf_stride, &full[b], ti * bx * TX, tj * by * TY);
-      } else {
-        issue_tile_cp_async(a, buf0 + b * a.buf_stride, ti * bx * TX, tj * by * TY);
+    const int tiles_x = a.tiles_x;
+    const int n_tiles = (int)a.n_tiles;
+    const int step = gridDim.x;
+    const int step_x = step % tiles_x, step_y = step / tiles_x;
+    auto advance = [&](int& tx_, int& ty_) {
+      tx_ += step_x;
+      ty_ += step_y;
+      if (tx_ >= tiles_x) {
+        tx_ -= tiles_x;
+        ++ty_;
       }
     };
-    if (tma && leader) {
-      mbar_init(&full[0]);
-      mbar_init(&full[1]);
-      mbar_init_fence();
+    auto issue = [&](int tx_, int ty_, int b) {
+      if (tma) {
+        if (leader)
+          issue_tile_tma(a, buf0 + b * a.buf_stride, &full[b], tx_ * bx * TX, ty_ * by * TY);
+      } else {
+        issue_tile_cp_async(a, buf0 + b * a.buf_stride, tx_ * bx * TX, ty_ * by * TY);
+      }
+    };
+    if (leader) {
+      s_fail = 0;
+      if (tma) {
+        mbar_init(&full[0]);
+        mbar_init(&full[1]);
+        mbar_init_fence();
+      }
     }
     __syncthreads();
-    long long t = blockIdx.x;
-    if (t < a.n_tiles) issue(t, 0);
+    int t = blockIdx.x;
+    int cx = t % tiles_x, cy = t / tiles_x;  // tile being computed
+    int nx = cx, ny = cy;                    // tile whose copy is issued next
+    if (t < n_tiles) issue(nx, ny, 0);
     if (!tma) cp_async_commit();
-    if (t + step < a.n_tiles) issue(t + step, 1);
+    advance(nx, ny);
+    if (t + step < n_tiles) issue(nx, ny, 1);
     if (!tma) cp_async_commit();
-    for (int it = 0; t < a.n_tiles; t += step, ++it) {
+    advance(nx, ny);
+    for (int it = 0; t < n_tiles; t += step, ++it) {
       const int b = it & 1;
       if (tma) {
-        const bool ok = mbar_wait(&full[b], (unsigned)(it >> 1) & 1u);
-        // every thread takes the same decision, so no thread is left at a barrier
-        if (__syncthreads_or(!ok)) {
-          if (leader && a.status) atomicOr(a.status, kStatusTmaTimeout);
-          return;
-        }
+        // a wait that gives up is reported at the barrier after the tile
+        if (!mbar_wait(&full[b], (unsigned)(it >> 1) & 1u)) s_fail = 1;
       } else {
         cp_async_wait_one();
         __syncthreads();
       }
-      const int ti = (int)(t % a.tiles_x), tj = (int)(t / a.tiles_x);
-      const int x0 = ti * bx * TX + threadIdx.x * TX;
-      const int y0 = tj * by * TY + threadIdx.y * TY;
+      const int x0 = cx * bx * TX + threadIdx.x * TX;
+      const int y0 = cy * by * TY + threadIdx.y * TY;
       const float* sbase =
           buf0 + b * a.buf_stride + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
       accumulate_tile<K, TX, TY>(
@@ -391,9 +405,15 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
         if (y < a.out_h)
           store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[r]);
       }
-      __syncthreads();  // buffer b is free
-      if (t + 2 * step < a.n_tiles) issue(t + 2 * step, b);
+      __syncthreads();  // buffer b is free; every thread sees s_fail
+      if (s_fail) {
+        if (leader && a.status) atomicOr(a.status, kStatusTmaTimeout);
+        return;
+      }
+      if (t + 2 * step < n_tiles) issue(nx, ny, b);
       if (!tma) cp_async_commit();
+      advance(nx, ny);
+      advance(cx, cy);
     }
   } else {
     if constexpr (FILT_SMEM) __syncthreads();

@@ -260,6 +260,9 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
       L.tiles_x = (p.out_w + c.block_x * c.tile_x - 1) / (c.block_x * c.tile_x);
       L.n_tiles = (long long)L.tiles_x *
                   ((p.out_h + c.block_y * c.tile_y - 1) / (c.block_y * c.tile_y));
+      // the persistent loop indexes tiles with 32-bit integers
+      if (L.n_tiles + (1LL << 22) > (long long)INT_MAX)
+        return fail(CT_ECONFIG, "too many tiles for the persistent loop");
       if (c.staging == CT_STAGE_TMA) {
         if (L.tile_w > 256 || L.tile_h > 256)
           return fail(CT_ECONFIG, "TMA box wider or taller than 256 elements");
