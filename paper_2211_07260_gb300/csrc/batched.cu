@@ -19,107 +19,59 @@ namespace convtune {
 
 __global__ void __launch_bounds__(kBatchThreads) batched_conv_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* const area0 = reinterpret_cast<float*>(smem_raw);  // area b: area0 + b * stride
-  __shared__ long long s_w[2];
-  __shared__ int s_img[2];
-  // thread 0: take the next work item and find its image (-1: none left)
-  auto grab = [&](int slot) {
-    const long long w = (long long)atomicAdd(a.counter, 1u);
-    int img = -1;
-    if (w < a.n_items) {
-      int lo = 0, hi = a.n_images - 1;  // last image whose first item is <= w
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (a.images[mid].first_item <= w) lo = mid;
-        else hi = mid - 1;
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  __shared__ long long s_item;
+  __shared__ int s_img;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long w = (long long)atomicAdd(a.counter, 1u);
+      int img = -1;
+      if (w < a.n_items) {
+        // last image whose first item is <= w
+        int lo = 0, hi = a.n_images - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (a.images[mid].first_item <= w) lo = mid;
+          else hi = mid - 1;
+        }
+        img = lo;
       }
-      img = lo;
+      s_item = w;
+      s_img = img;
     }
-    s_w[slot] = w;
-    s_img[slot] = img;
-  };
-  // all threads: start the copies of the item in `slot` into area `slot`
-  auto stage = [&](int slot) {
-    const long long w = s_w[slot];
-    if (w >= a.n_items) return;
-    const BatchImage& im = a.images[s_img[slot]];
-    const long long tl = w - im.first_item;
-    if (tl < 0 || tl >= (long long)im.tiles_x * im.tiles_y) return;
-    const int t = (int)tl;  // tiles of one image fit in 32 bits
-    float* area = area0 + slot * a.stage_stride;
-#define CT_BATCH_STAGE(KK)                                  \
-  case KK:                                                  \
-    if (im.ty == 1) batch_stage<KK, 1>(im, t, area);        \
-    else if (im.ty == 2) batch_stage<KK, 2>(im, t, area);   \
-    else batch_stage<KK, 4>(im, t, area);                   \
-    break;
-    switch (im.k) {
-      CT_BATCH_STAGE(1)
-      CT_BATCH_STAGE(3)
-      CT_BATCH_STAGE(5)
-      CT_BATCH_STAGE(7)
-      CT_BATCH_STAGE(9)
-      CT_BATCH_STAGE(11)
-      CT_BATCH_STAGE(13)
-      CT_BATCH_STAGE(15)
-      CT_BATCH_STAGE(17)
-      default: break;
-    }
-#undef CT_BATCH_STAGE
-  };
-
-  if (threadIdx.x == 0) {
-    grab(0);
-    grab(1);
-  }
-  __syncthreads();
-  stage(0);
-  cp_async_commit();
-  stage(1);
-  cp_async_commit();
-  for (int it = 0;; ++it) {
-    const int b = it & 1;
-    // read this item's descriptor before the barrier: thread 0 reuses the
-    // slot for a later item once everyone is past it
-    const long long w = s_w[b];
-    const int img = s_img[b];
+    __syncthreads();
+    const long long w = s_item;
+    const int img = s_img;
+    __syncthreads();  // s_item / s_img are rewritten only after this point
     if (w >= a.n_items) break;
-    cp_async_wait_one();
-    __syncthreads();  // area b has landed for every thread's copies
-    if (threadIdx.x == 0) grab(b);
     const BatchImage& im = a.images[img];
     const long long tl = w - im.first_item;
-    const bool ok = tl >= 0 && tl < (long long)im.tiles_x * im.tiles_y;
-    if (!ok) {
+    if (tl < 0 || tl >= (long long)im.tiles_x * im.tiles_y) {
       if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
-    } else {
-      const int t = (int)tl;
-      const float* area = area0 + b * a.stage_stride;
-#define CT_BATCH_CASE(KK)                                        \
-  case KK:                                                       \
-    if (im.ty == 1) batch_compute<KK, 1>(im, t, area);           \
-    else if (im.ty == 2) batch_compute<KK, 2>(im, t, area);      \
-    else batch_compute<KK, 4>(im, t, area);                      \
-    break;
-      switch (im.k) {
-        CT_BATCH_CASE(1)
-        CT_BATCH_CASE(3)
-        CT_BATCH_CASE(5)
-        CT_BATCH_CASE(7)
-        CT_BATCH_CASE(9)
-        CT_BATCH_CASE(11)
-        CT_BATCH_CASE(13)
-        CT_BATCH_CASE(15)
-        CT_BATCH_CASE(17)
-        default:
-          if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
-          break;
-      }
-#undef CT_BATCH_CASE
+      continue;
     }
-    __syncthreads();  // area b is free and the new descriptor in slot b is visible
-    stage(b);
-    cp_async_commit();
+    const int t = (int)tl;  // tiles of one image fit in 32 bits
+#define CT_BATCH_CASE(KK)                                   \
+  case KK:                                                  \
+    if (im.ty == 1) batch_tile<KK, 1>(im, t, smem);         \
+    else if (im.ty == 2) batch_tile<KK, 2>(im, t, smem);    \
+    else batch_tile<KK, 4>(im, t, smem);                    \
+    break;
+    switch (im.k) {
+      CT_BATCH_CASE(1)
+      CT_BATCH_CASE(3)
+      CT_BATCH_CASE(5)
+      CT_BATCH_CASE(7)
+      CT_BATCH_CASE(9)
+      CT_BATCH_CASE(11)
+      CT_BATCH_CASE(13)
+      CT_BATCH_CASE(15)
+      CT_BATCH_CASE(17)
+      default:
+        if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
+        break;
+    }
+#undef CT_BATCH_CASE
   }
 }
 
@@ -127,7 +79,6 @@ namespace {
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Bytes of one staging area (taps + halo tile) for an image's bucket.
 size_t batch_smem_bytes(int k, int bx, int ty) {
   const int kp = round_up(k, 4);
   const int filt = round_up(k * kp, 32);
@@ -136,10 +87,6 @@ size_t batch_smem_bytes(int k, int bx, int ty) {
   const int tile_h = by * ty + k - 1;
   return sizeof(float) * (size_t)(filt + tile_w * tile_h);
 }
-
-// Two staging areas of the largest per-area need, each 128-byte aligned.
-int stage_stride_floats(size_t area_bytes) { return (int)((area_bytes + 127) / 128 * 32); }
-size_t dynamic_smem(size_t area_bytes) { return 2 * sizeof(float) * (size_t)stage_stride_floats(area_bytes); }
 
 bool valid_tile(int bx, int ty) {
   return (bx == 16 || bx == 32 || bx == 64 || bx == 128) && (ty == 1 || ty == 2 || ty == 4);
@@ -193,8 +140,7 @@ int enqueue_batch(ct_batch* b, cudaStream_t s) {
   a.n_items = b->n_items;
   a.counter = b->d_counter;
   a.status = status;
-  a.stage_stride = stage_stride_floats(b->smem);
-  batched_conv_kernel<<<b->grid, kBatchThreads, dynamic_smem(b->smem), s>>>(a);
+  batched_conv_kernel<<<b->grid, kBatchThreads, b->smem, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -321,7 +267,7 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
   if ((e = cudaMalloc(&b->d_counter, 256)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(b->d_counter, 0, 256)) != cudaSuccess) return cuda_status(e);
   // persistent grid: resident CTAs per SM x SMs, capped by the work
-  if (dynamic_smem(b->smem) > 48 * 1024) {
+  if (b->smem > 48 * 1024) {
     // the cap is per kernel and shared by every plan: raise it to the device
     // limit (a per-plan value could undercut another live plan's graph)
     int optin = 0;
@@ -331,15 +277,14 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
     cudaFuncAttributes fa;
     if ((e = cudaFuncGetAttributes(&fa, batched_conv_kernel)) != cudaSuccess)
       return cuda_status(e);
-    if (dynamic_smem(b->smem) + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
+    if (b->smem + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
     e = cudaFuncSetAttribute(batched_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              optin - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return cuda_status(e);
   }
   int per_sm = 0, sms = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
-                                                         kBatchThreads, dynamic_smem(b->smem))) !=
-      cudaSuccess)
+                                                         kBatchThreads, b->smem)) != cudaSuccess)
     return cuda_status(e);
   if (per_sm < 1) return CT_ECONFIG;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device)) != cudaSuccess)
@@ -408,7 +353,7 @@ int ct_batch_info(const ct_batch* b, ct_batch_stats* st) {
   st->n_images = (int)b->host_images.size();
   st->n_items = b->n_items;
   st->grid = b->grid;
-  st->smem_bytes = (long)dynamic_smem(b->smem);
+  st->smem_bytes = (long)b->smem;
   st->flop = b->flop;
   for (const BatchImage& im : b->host_images)
     st->bytes += 4.0 * ((double)im.in_h * im.in_w + (double)im.out_h * im.out_w + im.k * im.k);
@@ -661,8 +606,7 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
     return cuda_status(e);
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
-                                                         kBatchThreads, dynamic_smem(smem))) !=
-      cudaSuccess)
+                                                         kBatchThreads, smem)) != cudaSuccess)
     return cuda_status(e);
   if (per_sm < 1) return CT_ECONFIG;
   BatchArgs a;
@@ -671,9 +615,8 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   a.n_items = first;
   a.counter = counter;
   a.status = status;
-  a.stage_stride = stage_stride_floats(smem);
   const int grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * nd.sms, first));
-  batched_conv_kernel<<<grid, kBatchThreads, dynamic_smem(smem), s>>>(a);
+  batched_conv_kernel<<<grid, kBatchThreads, smem, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -715,10 +658,7 @@ int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, 
   return CT_OK;
 }
 
-int launch_batched_kernel(const BatchArgs& args, size_t smem, int sms, cudaStream_t s) {
-  BatchArgs a = args;
-  a.stage_stride = stage_stride_floats(smem);
-  smem = dynamic_smem(smem);
+int launch_batched_kernel(const BatchArgs& a, size_t smem, int sms, cudaStream_t s) {
   static std::once_flag once;
   static cudaError_t raised = cudaSuccess;
   std::call_once(once, [] {

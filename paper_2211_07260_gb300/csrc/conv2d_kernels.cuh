@@ -309,7 +309,7 @@ __device__ __forceinline__ void accumulate_tile(float (&acc)[TY][TX], FetchRow&&
 //   STAGED    = false: DIRECT staging; true: SMEM or TMA (args.staging)
 //   FILT_SMEM = false: taps from the parameter (constant) space
 // Dynamic shared memory: [filter K x KP (if FILT_SMEM), padded to 32 floats]
-//                        [tile tile_h x smem_pitch (if STAGED)] [mbarrier]
+//                        [staging buffer 0] [staging buffer 1 (persistent)]
 // ----------------------------------------------------------------------------
 template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM>
 __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
@@ -339,7 +339,7 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
     // freed buffer is refilled with the tile after that.  Tile coordinates
     // advance by adding the grid stride (no divisions in the loop).
     float* const buf0 = sfilt + kFiltFloats;  // buffer b starts at buf0 + b * buf_stride
-    uint64_t* full = reinterpret_cast<uint64_t*>(sfilt + kFiltFloats + 2 * a.buf_stride);
+    __shared__ __align__(8) uint64_t full[2];  // TMA completion barriers
     __shared__ int s_fail;
     const bool tma = a.staging == kStageTma;
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;

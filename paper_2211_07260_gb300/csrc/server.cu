@@ -157,12 +157,11 @@ struct ct_server {
 int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
   cudaError_t e;
   int rc = CT_OK;
-  // inputs in: the columns the kernel reads, rows at the caller's pitch
+  // inputs in: whole pitched rows in one contiguous copy (the pool's copy of
+  // the caller's padding columns is never read)
   for (Request* r : batch) {
-    const size_t pitch = sizeof(float) * (size_t)r->in_pitch;
-    e = cudaMemcpy2DAsync(pool + r->off, pitch, r->in_host, pitch,
-                          sizeof(float) * (size_t)(r->out_w + r->k - 1), r->out_h + r->k - 1,
-                          cudaMemcpyHostToDevice, sl.s);
+    const size_t bytes = sizeof(float) * (size_t)r->in_pitch * (r->out_h + r->k - 1);
+    e = cudaMemcpyAsync(pool + r->off, r->in_host, bytes, cudaMemcpyHostToDevice, sl.s);
     if (e != cudaSuccess) return cuda_status(e);
   }
   if (opt.plain) {
@@ -248,8 +247,13 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
   // padding columns are left untouched)
   for (Request* r : batch) {
     const size_t pitch = sizeof(float) * (size_t)r->out_pitch;
-    e = cudaMemcpy2DAsync(r->out_host, pitch, pool + r->off + r->in_bytes, pitch,
-                          sizeof(float) * (size_t)r->out_w, r->out_h, cudaMemcpyDeviceToHost, sl.s);
+    if (r->out_pitch == r->out_w)  // no padding columns: one contiguous copy
+      e = cudaMemcpyAsync(r->out_host, pool + r->off + r->in_bytes, pitch * r->out_h,
+                          cudaMemcpyDeviceToHost, sl.s);
+    else
+      e = cudaMemcpy2DAsync(r->out_host, pitch, pool + r->off + r->in_bytes, pitch,
+                            sizeof(float) * (size_t)r->out_w, r->out_h, cudaMemcpyDeviceToHost,
+                            sl.s);
     if (e != cudaSuccess) return cuda_status(e);
   }
   if ((e = cudaEventRecord(sl.ev, sl.s)) != cudaSuccess) return cuda_status(e);
