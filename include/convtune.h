@@ -558,6 +558,34 @@ int ct_server_stats_get(ct_server* sv, int reset, ct_server_stats* out);
 /* Finish every queued request, stop the worker and free the server. */
 int ct_server_destroy(ct_server* sv);
 
+
+/* ---- analyses of tuning records (Sections IV-A, IV-B) ------------------- */
+
+/*
+ * The five tuning methods compared in Section IV-A, over records of a
+ * configuration x clock sweep (invalid records ignored): out[0] race-to-idle
+ * (fastest point), out[1] least energy at the highest clock, out[2] the
+ * fastest configuration at the highest clock then its least-energy clock,
+ * out[3] the least-energy configuration at the base clock (the sampled clock
+ * nearest base_clock_mhz) then its least-energy clock, out[4] global least
+ * energy.  Indices into recs; ties as ct_select_best.
+ */
+int ct_tuning_methods(const ct_record* recs, int n, int base_clock_mhz, int out[5]);
+/* Pareto front of (GFLOP/s, GFLOP/J), both maximised: indices of records no
+   other record dominates, by GFLOP/s descending (ties: GFLOP/J, index). */
+int ct_pareto_front(const ct_record* recs, int n, int* out_idx, int cap, int* n_out);
+/*
+ * Proportion of PageRank centrality (Section IV-B): nodes are the records;
+ * two are neighbours when they differ in exactly one parameter (the seven
+ * configuration fields and the clock); an edge leads to each neighbour of
+ * strictly better fitness (time or energy); PageRank with the given damping
+ * (0.85 in common use), walkers at minima restarting uniformly.  For each
+ * p >= 1, out_prop = centrality of minima with fitness <= p * optimum over
+ * centrality of all minima.
+ */
+int ct_centrality(const ct_record* recs, int n, int objective, double damping, const double* ps,
+                  int n_p, double* out_prop);
+
 #ifdef __cplusplus
 }
 #endif

@@ -201,6 +201,9 @@ _SIGS = {
     "ct_server_stats_get": (c_int, [c_void_p, c_int, c_void_p]),
     "ct_server_destroy": (c_int, [c_void_p]),
     "ct_read_sensors": (c_int, [c_void_p]),
+    "ct_tuning_methods": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "ct_pareto_front": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p]),
+    "ct_centrality": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p, c_int, c_void_p]),
     "ct_tune_steered": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                 c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                 c_void_p, c_int, c_void_p, c_void_p]),
@@ -718,3 +721,45 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---- analyses of tuning records ---------------------------------------------
+METHODS = ("race_to_idle", "energy_maxclock", "race_to_idle_clocks", "energy_clocks",
+           "global_energy")
+
+
+def _record_array(records):
+    arr = (CtRecord * len(records))()
+    for i, r in enumerate(records):
+        for k, _ in CtRecord._fields_:
+            if k == "cfg":
+                arr[i].cfg = Config(*r["cfg"]).to_c()
+            else:
+                setattr(arr[i], k, r[k])
+    return arr
+
+
+def tuning_methods(records, base_clock_mhz: int) -> dict:
+    """The five tuning methods of Section IV-A (ct_tuning_methods)."""
+    out = (c_int * 5)()
+    _check(lib().ct_tuning_methods(_record_array(records), len(records), int(base_clock_mhz),
+                                   out), "ct_tuning_methods")
+    return {m: out[i] for i, m in enumerate(METHODS)}
+
+
+def pareto_front(records) -> list:
+    idx = (c_int * max(1, len(records)))()
+    n = c_int(0)
+    _check(lib().ct_pareto_front(_record_array(records), len(records), idx, len(idx),
+                                 ctypes.byref(n)), "ct_pareto_front")
+    return [idx[i] for i in range(n.value)]
+
+
+def centrality(records, objective="energy", ps=(1.0, 1.05, 1.1, 1.25, 1.5, 2.0),
+               damping=0.85) -> dict:
+    p = np.ascontiguousarray(ps, dtype=np.float64)
+    out = np.zeros_like(p)
+    obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
+    _check(lib().ct_centrality(_record_array(records), len(records), obj, float(damping),
+                               p.ctypes.data, p.size, out.ctypes.data), "ct_centrality")
+    return dict(zip(ps, out.tolist()))

@@ -160,7 +160,11 @@ int load_cache(const char* path, std::map<std::string, ct_record>* out) {
 
 double key_energy(const ct_record& r) { return isnan(r.energy_j) ? INFINITY : r.energy_j; }
 
-bool better(const ct_record& a, const ct_record& b, int objective) {
+}  // namespace
+
+// The selection order of the tuner (ties: shorter time, lower clock,
+// lexicographically smaller configuration).
+bool record_better(const ct_record& a, const ct_record& b, int objective) {
   auto cfg = [](const ct_record& r) {
     return std::make_tuple(r.cfg.block_x, r.cfg.block_y, r.cfg.tile_x, r.cfg.tile_y,
                            r.cfg.staging, r.cfg.filter_mem, r.cfg.vec_width);
@@ -178,8 +182,6 @@ bool better(const ct_record& a, const ct_record& b, int objective) {
          std::make_tuple(key_energy(b), b.t_s, b.clock_mhz_req, cfg(b));
 }
 
-}  // namespace
-
 int select_best(const ct_record* recs, int n, int objective, const int* clocks, int n_clocks) {
   int best = -1;
   for (int i = 0; i < n; ++i) {
@@ -191,7 +193,7 @@ int select_best(const ct_record* recs, int n, int objective, const int* clocks, 
       for (int k = 0; k < n_clocks; ++k) in |= clocks[k] == r.clock_mhz_req;
       if (!in) continue;
     }
-    if (best < 0 || better(r, recs[best], objective)) best = i;
+    if (best < 0 || record_better(r, recs[best], objective)) best = i;
   }
   return best;
 }
