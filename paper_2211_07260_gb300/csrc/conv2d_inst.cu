@@ -70,17 +70,10 @@ cudaError_t CT_CAT(launch_k, CT_K)(const ConvLaunch& L, cudaStream_t s) {
   a.smem_pitch = L.smem_pitch;
   a.tile_w = L.tile_w;
   a.tile_h = L.tile_h;
-  a.buf_stride = L.buf_stride;
-  a.tiles_x = L.tiles_x;
-  a.n_tiles = L.n_tiles;
   memcpy(a.w, L.taps, sizeof(float) * K * K);
   const dim3 block(L.bx, L.by);
-  // staged variants are persistent (1-D grid of resident CTAs); direct
-  // variants take one tile per CTA
-  const dim3 grid = L.staging != kStageDirect
-                        ? dim3(L.grid_x)
-                        : dim3((L.out_w + L.bx * L.tx - 1) / (L.bx * L.tx),
-                               (L.out_h + L.by * L.ty - 1) / (L.by * L.ty));
+  const dim3 grid((L.out_w + L.bx * L.tx - 1) / (L.bx * L.tx),
+                  (L.out_h + L.by * L.ty - 1) / (L.by * L.ty));
   void* args[] = {&a};
   return cudaLaunchKernel(fn, grid, block, args, L.smem_bytes, s);
 }

@@ -13,11 +13,10 @@
 //   staging           DIRECT: each thread reads its rows straight from global
 //                     memory (vector loads through L1), the horizontal halo of
 //                     a row comes from neighbouring lanes by warp shuffles;
-//                     one tile per CTA.
-//                     SMEM / TMA: persistent CTAs, each tile's halo copied to
-//                     one of two shared-memory buffers with cp.async (SMEM) or
-//                     one 2-D cp.async.bulk.tensor completing on an mbarrier
-//                     (TMA), the next tile's copy in flight during compute
+//                     SMEM: the CTA's halo tile is copied to shared memory with
+//                     cp.async; TMA: the same tile arrives by one 2-D
+//                     cp.async.bulk.tensor copy completing on an mbarrier.
+//                     One output tile per CTA in every mode.
 //   filter memory     CONST: taps are read from the kernel's parameter space
 //                     (constant bank, an immediate FFMA operand once the tap
 //                     loops are unrolled); SHARED: taps are copied to shared
@@ -48,9 +47,6 @@ struct alignas(64) ConvArgs {
   int staging;               // kStageDirect / kStageSmem / kStageTma
   int smem_pitch;            // floats per shared-memory tile row
   int tile_w, tile_h;        // staged tile (floats); tile_w % 4 == 0
-  int buf_stride;            // floats between the two staging buffers (% 32 == 0)
-  int tiles_x;               // output tiles per row of tiles (staged variants)
-  long long n_tiles;         // output tiles in total (staged variants)
   float w[NTAPS];            // taps, row-major fh x fw
 };
 
@@ -309,7 +305,7 @@ __device__ __forceinline__ void accumulate_tile(float (&acc)[TY][TX], FetchRow&&
 //   STAGED    = false: DIRECT staging; true: SMEM or TMA (args.staging)
 //   FILT_SMEM = false: taps from the parameter (constant) space
 // Dynamic shared memory: [filter K x KP (if FILT_SMEM), padded to 32 floats]
-//                        [staging buffer 0] [staging buffer 1 (persistent)]
+//                        [staged tile tile_h x smem_pitch (if STAGED)]
 // ----------------------------------------------------------------------------
 template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM>
 __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
@@ -333,87 +329,42 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
   float acc[TY][TX];
 
   if constexpr (STAGED) {
-    // Persistent CTAs walk the tiles t = blockIdx.x, blockIdx.x + gridDim.x,
-    // ... with two staging buffers: while tile t is computed from one, the
-    // copy of the next tile is already in flight into the other, and the
-    // freed buffer is refilled with the tile after that.  Tile coordinates
-    // advance by adding the grid stride (no divisions in the loop).
-    float* const buf0 = sfilt + kFiltFloats;  // buffer b starts at buf0 + b * buf_stride
-    __shared__ __align__(8) uint64_t full[2];  // TMA completion barriers
-    __shared__ int s_fail;
-    const bool tma = a.staging == kStageTma;
+    // One tile per CTA: the halo tile is copied to shared memory (cp.async,
+    // or one 2-D TMA box completing on an mbarrier), then computed.
+    __shared__ __align__(8) uint64_t full;  // TMA completion barrier
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-    const int tiles_x = a.tiles_x;
-    const int n_tiles = (int)a.n_tiles;
-    const int step = gridDim.x;
-    const int step_x = step % tiles_x, step_y = step / tiles_x;
-    auto advance = [&](int& tx_, int& ty_) {
-      tx_ += step_x;
-      ty_ += step_y;
-      if (tx_ >= tiles_x) {
-        tx_ -= tiles_x;
-        ++ty_;
-      }
-    };
-    auto issue = [&](int tx_, int ty_, int b) {
-      if (tma) {
-        if (leader)
-          issue_tile_tma(a, buf0 + b * a.buf_stride, &full[b], tx_ * bx * TX, ty_ * by * TY);
-      } else {
-        issue_tile_cp_async(a, buf0 + b * a.buf_stride, tx_ * bx * TX, ty_ * by * TY);
-      }
-    };
-    if (leader) {
-      s_fail = 0;
-      if (tma) {
-        mbar_init(&full[0]);
-        mbar_init(&full[1]);
+    const int gx0 = blockIdx.x * bx * TX, gy0 = blockIdx.y * by * TY;
+    float* const tile = sfilt + kFiltFloats;
+    if (a.staging == kStageTma) {
+      if (leader) {
+        mbar_init(&full);
         mbar_init_fence();
       }
-    }
-    __syncthreads();
-    int t = blockIdx.x;
-    int cx = t % tiles_x, cy = t / tiles_x;  // tile being computed
-    int nx = cx, ny = cy;                    // tile whose copy is issued next
-    if (t < n_tiles) issue(nx, ny, 0);
-    if (!tma) cp_async_commit();
-    advance(nx, ny);
-    if (t + step < n_tiles) issue(nx, ny, 1);
-    if (!tma) cp_async_commit();
-    advance(nx, ny);
-    for (int it = 0; t < n_tiles; t += step, ++it) {
-      const int b = it & 1;
-      if (tma) {
-        // a wait that gives up is reported at the barrier after the tile
-        if (!mbar_wait(&full[b], (unsigned)(it >> 1) & 1u)) s_fail = 1;
-      } else {
-        cp_async_wait_one();
-        __syncthreads();
-      }
-      const int x0 = cx * bx * TX + threadIdx.x * TX;
-      const int y0 = cy * by * TY + threadIdx.y * TY;
-      const float* sbase =
-          buf0 + b * a.buf_stride + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
-      accumulate_tile<K, TX, TY>(
-          acc, [&](int r, float(&rowv)[TX + K - 1]) {
-            fetch_row_smem<K, TX>(rowv, sbase + r * a.smem_pitch);
-          },
-          tap);
-#pragma unroll
-      for (int r = 0; r < TY; ++r) {
-        const int y = y0 + r;
-        if (y < a.out_h)
-          store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[r]);
-      }
-      __syncthreads();  // buffer b is free; every thread sees s_fail
-      if (s_fail) {
+      __syncthreads();
+      if (leader) issue_tile_tma(a, tile, &full, gx0, gy0);
+      const bool ok = mbar_wait(&full, 0u);
+      // every thread takes the same decision, so no thread is left at a barrier
+      if (__syncthreads_or(!ok)) {
         if (leader && a.status) atomicOr(a.status, kStatusTmaTimeout);
         return;
       }
-      if (t + 2 * step < n_tiles) issue(nx, ny, b);
-      if (!tma) cp_async_commit();
-      advance(nx, ny);
-      advance(cx, cy);
+    } else {
+      issue_tile_cp_async(a, tile, gx0, gy0);
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    const int x0 = gx0 + threadIdx.x * TX;
+    const int y0 = gy0 + threadIdx.y * TY;
+    const float* sbase = tile + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
+    accumulate_tile<K, TX, TY>(
+        acc, [&](int r, float(&rowv)[TX + K - 1]) {
+          fetch_row_smem<K, TX>(rowv, sbase + r * a.smem_pitch);
+        },
+        tap);
+#pragma unroll
+    for (int r = 0; r < TY; ++r) {
+      const int y = y0 + r;
+      if (y < a.out_h) store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[r]);
     }
   } else {
     if constexpr (FILT_SMEM) __syncthreads();

@@ -32,10 +32,6 @@ struct ConvLaunch {
   int bx, by, tx, ty;
   int staging, filt_smem, vw;
   int smem_pitch, tile_w, tile_h;
-  int buf_stride;          // staged: floats between the two staging buffers
-  int tiles_x;             // staged: tiles per row of tiles
-  long long n_tiles;       // staged: tiles in total
-  int grid_x;              // staged: persistent CTAs (1-D grid)
   size_t smem_bytes;
   const CUtensorMap* tmap; // valid when staging == TMA
 };

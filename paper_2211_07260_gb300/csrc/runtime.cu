@@ -24,8 +24,6 @@ struct DeviceState {
   unsigned* status = nullptr;
   int smem_optin = 0;
   int sm_count = 0;
-  // resident CTAs per SM of (kernel, threads, dynamic shared memory)
-  std::map<std::tuple<const void*, int, size_t>, int> occupancy;
   std::set<const void*> smem_raised;  // kernels whose dynamic shared-memory cap is raised
   // buffers of the host-buffer entry point
   float* din = nullptr;
@@ -257,12 +255,6 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
     if (staged) {
       L.tile_w = round_up(c.block_x * c.tile_x + K - 1, 4);
       L.tile_h = c.block_y * c.tile_y + K - 1;
-      L.tiles_x = (p.out_w + c.block_x * c.tile_x - 1) / (c.block_x * c.tile_x);
-      L.n_tiles = (long long)L.tiles_x *
-                  ((p.out_h + c.block_y * c.tile_y - 1) / (c.block_y * c.tile_y));
-      // the persistent loop indexes tiles with 32-bit integers
-      if (L.n_tiles + (1LL << 22) > (long long)INT_MAX)
-        return fail(CT_ECONFIG, "too many tiles for the persistent loop");
       if (c.staging == CT_STAGE_TMA) {
         if (L.tile_w > 256 || L.tile_h > 256)
           return fail(CT_ECONFIG, "TMA box wider or taller than 256 elements");
@@ -276,16 +268,11 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
         if (c.block_x == 16 && c.tile_x == 1)
           while (L.smem_pitch % 32 != 16) L.smem_pitch += 4;
       }
-      // staging buffers start on 128-byte boundaries; two mbarriers follow.
-      // smem_bytes is the persistent (two-buffer) size; the planner below
-      // falls back to one buffer when two would cost resident CTAs
-      L.buf_stride = round_up(L.tile_h * L.smem_pitch, 32);
-      smem += 2 * sizeof(float) * (size_t)L.buf_stride;
+      smem += sizeof(float) * (size_t)L.tile_h * L.smem_pitch;
     }
     L.smem_bytes = smem;
   }
-  const bool persistent = plan->specialised && L.staging != kStageDirect;
-  if (!persistent && plan->grid.y > 65535u) return fail(CT_ECONFIG, "grid y exceeds 65535");
+  if (plan->grid.y > 65535u) return fail(CT_ECONFIG, "grid y exceeds 65535");
 
   if (!device_checks) return CT_OK;
   // device-dependent checks
@@ -297,55 +284,10 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
   if (e != cudaSuccess) return fail(cuda_status(e), "cudaFuncGetAttributes failed");
   if (c.block_x * c.block_y > fa.maxThreadsPerBlock)
     return fail(CT_ECONFIG, "block larger than the kernel's register budget allows");
-  // staged variants need at least one buffer to fit (two for persistence)
-  const size_t smem_min = (specialised && L.staging != kStageDirect)
-                              ? L.smem_bytes - sizeof(float) * (size_t)L.buf_stride
-                              : L.smem_bytes;
-  if (smem_min + fa.sharedSizeBytes > (size_t)st->smem_optin)
+  if (L.smem_bytes + fa.sharedSizeBytes > (size_t)st->smem_optin)
     return fail(CT_ECONFIG, "shared memory exceeds the per-block limit");
   if (c.staging == CT_STAGE_TMA && specialised && !tensor_map_encoder())
     return fail(CT_ENOTSUP, "cuTensorMapEncodeTiled unavailable");
-  if (persistent) {
-    // Two staging buffers let a persistent CTA overlap the next tile's copy
-    // with compute, but double the shared memory per CTA.  Use them only when
-    // they cost no resident CTAs; otherwise launch one CTA per tile with one
-    // buffer (the same kernel: its tile loop then runs once).
-    const int threads = c.block_x * c.block_y;
-    const size_t smem2 = L.smem_bytes;
-    const size_t smem1 = smem2 - sizeof(float) * (size_t)L.buf_stride;
-    auto occupancy = [&](size_t bytes, int* per_sm) -> int {
-      std::lock_guard<std::mutex> lk(g_mu);
-      auto key = std::make_tuple(plan->fn, threads, bytes);
-      auto it = st->occupancy.find(key);
-      if (it != st->occupancy.end()) {
-        *per_sm = it->second;
-        return CT_OK;
-      }
-      if (bytes > 48 * 1024) {
-        const cudaError_t e2 = raise_smem_cap(st, plan->fn);
-        if (e2 != cudaSuccess) return cuda_status(e2);
-      }
-      const cudaError_t e2 =
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, plan->fn, threads, bytes);
-      if (e2 != cudaSuccess) return cuda_status(e2);
-      st->occupancy[key] = *per_sm;
-      return CT_OK;
-    };
-    int occ1 = 0, occ2 = 0;
-    int orc = occupancy(smem1, &occ1);
-    if (orc == CT_OK && smem2 + fa.sharedSizeBytes <= (size_t)st->smem_optin)
-      orc = occupancy(smem2, &occ2);
-    if (orc != CT_OK) return fail(orc, "occupancy query failed");
-    if (occ1 < 1) return fail(CT_ECONFIG, "no CTA of this configuration fits on an SM");
-    if (occ2 >= occ1) {
-      const long long resident = (long long)occ2 * st->sm_count;
-      L.grid_x = (int)std::max(1LL, std::min(resident, L.n_tiles));
-    } else {
-      L.smem_bytes = smem1;
-      L.grid_x = (int)L.n_tiles;
-    }
-    plan->grid = dim3(L.grid_x);
-  }
   return CT_OK;
 }
 
