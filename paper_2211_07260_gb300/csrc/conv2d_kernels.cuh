@@ -30,6 +30,7 @@
 
 #include "conv2d_launch.h"
 
+
 namespace convtune {
 
 // Launch arguments.  The filter travels by value in the parameter space, i.e.
@@ -301,6 +302,53 @@ __device__ __forceinline__ void accumulate_tile(float (&acc)[TY][TX], FetchRow&&
 }
 
 // ----------------------------------------------------------------------------
+// The same tap accumulation with the filter-row loop outermost: the TY input
+// rows that filter row j needs (rows j .. j+TY-1 relative to y0) live in a
+// ring of registers; after row j's taps, the ring slot of the row that is no
+// longer needed takes the next input row.  The j loop is a real loop over
+// blocks of TY rows (ring positions are then compile-time), so the code is
+// about K / TY times shorter than the fully unrolled form.  For a fixed output
+// the taps still arrive in (j, i) lexicographic order: bitwise the same
+// result.  ROWP(r) points at input row r (shared memory, 16-byte aligned);
+// TAPROW(j, w) fills w[0 .. K-1] with filter row j.
+// ----------------------------------------------------------------------------
+template <int K, int TX, int TY, class RowPtr, class TapRow>
+__device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPtr&& rowp,
+                                                     TapRow&& taprow) {
+  constexpr int N = TX + K - 1;
+  constexpr int KP = (K + 3) / 4 * 4;
+  float ring[TY][N];
+#pragma unroll
+  for (int t = 0; t < TY; ++t) {
+#pragma unroll
+    for (int x = 0; x < TX; ++x) acc[t][x] = 0.0f;
+    fetch_row_smem<K, TX>(ring[t], rowp(t));
+  }
+  constexpr int NB = (K + TY - 1) / TY;
+#pragma unroll 1
+  for (int jb = 0; jb < NB; ++jb) {
+#pragma unroll
+    for (int jj = 0; jj < TY; ++jj) {
+      const int j = jb * TY + jj;
+      if (j < K) {
+        float w[KP];
+        taprow(j, w);
+#pragma unroll
+        for (int t = 0; t < TY; ++t)
+#pragma unroll
+          for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int x = 0; x < TX; ++x)
+              acc[t][x] = fmaf(ring[(t + jj) % TY][x + i], w[i], acc[t][x]);
+        // slot jj held input row j (needed by output row 0 only); it now
+        // takes row j + TY, needed from filter row j + 1 on
+        if (j + 1 < K) fetch_row_smem<K, TX>(ring[jj], rowp(TY + j));
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Specialised kernel: square odd filter K x K.
 //   STAGED    = false: DIRECT staging; true: SMEM or TMA (args.staging)
 //   FILT_SMEM = false: taps from the parameter (constant) space
@@ -356,11 +404,36 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
     const int x0 = gx0 + threadIdx.x * TX;
     const int y0 = gy0 + threadIdx.y * TY;
     const float* sbase = tile + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
-    accumulate_tile<K, TX, TY>(
-        acc, [&](int r, float(&rowv)[TX + K - 1]) {
-          fetch_row_smem<K, TX>(rowv, sbase + r * a.smem_pitch);
-        },
-        tap);
+    // The fully unrolled form runs K*K*TX*TY FFMAs straight through; above
+    // ~2500 of them (4 x 4 tiles, K >= 13) its code no longer fits the
+    // instruction caches and warps stall on instruction fetch, so those
+    // variants take the ring form (measured on GB300: 17 x 17, 4 x 4 tiles,
+    // 54 -> 63 TFLOP/s; smaller bodies are faster unrolled).
+    if constexpr (TX * TY * K * K > 2500) {
+      accumulate_tile_ring<K, TX, TY>(
+          acc, [&](int r) { return sbase + r * a.smem_pitch; },
+          [&](int j, float(&w)[KP]) {
+            if constexpr (FILT_SMEM) {
+#pragma unroll
+              for (int i = 0; i < KP; i += 4) {
+                const float4 q = *reinterpret_cast<const float4*>(sfilt + j * KP + i);
+                w[i] = q.x;
+                w[i + 1] = q.y;
+                w[i + 2] = q.z;
+                w[i + 3] = q.w;
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < K; ++i) w[i] = a.w[j * K + i];
+            }
+          });
+    } else {
+      accumulate_tile<K, TX, TY>(
+          acc, [&](int r, float(&rowv)[TX + K - 1]) {
+            fetch_row_smem<K, TX>(rowv, sbase + r * a.smem_pitch);
+          },
+          tap);
+    }
 #pragma unroll
     for (int r = 0; r < TY; ++r) {
       const int y = y0 + r;
