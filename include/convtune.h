@@ -141,6 +141,15 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
  */
 int ct_status_read(unsigned* bits, int clear);
 
+/*
+ * Self-test of the bounded device waits: launches one CTA that waits on a
+ * barrier phase nothing completes, gives up after spin_limit polls
+ * (1 .. 2^24) and sets status bit 0 (as a TMA wait that gave up would); the
+ * context stays usable.  Asynchronous on `stream`; read the bit with
+ * ct_status_read().
+ */
+int ct_selftest_wait_timeout(unsigned spin_limit, void* stream);
+
 /* Device facts used for rooflines (current device). */
 typedef struct {
   int sm_count;

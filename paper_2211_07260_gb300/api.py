@@ -204,6 +204,7 @@ _SIGS = {
     "ct_tuning_methods": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "ct_pareto_front": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p]),
     "ct_centrality": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p, c_int, c_void_p]),
+    "ct_selftest_wait_timeout": (c_int, [ctypes.c_uint, c_void_p]),
     "ct_tune_steered": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                 c_double, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                 c_void_p, c_int, c_void_p, c_void_p]),

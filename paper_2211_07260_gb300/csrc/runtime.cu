@@ -469,3 +469,45 @@ int ct_device_info_get(ct_device_info* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded device wait used by TMA staging: one CTA waits on
+// an mbarrier phase that nothing completes, gives up after spin_limit polls
+// per thread and reports through the device status word, leaving the context
+// usable.
+// ---------------------------------------------------------------------------
+namespace convtune {
+namespace {
+
+__global__ void wait_timeout_selftest_kernel(unsigned* status, unsigned spin_limit) {
+  __shared__ __align__(8) uint64_t bar;
+  const unsigned addr = static_cast<unsigned>(__cvta_generic_to_shared(&bar));
+  if (threadIdx.x == 0) {
+    // expects one arrival that never comes
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(addr));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  unsigned done = 0;
+  for (unsigned it = 0; it < spin_limit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(0u)
+        : "memory");
+  }
+  if (__syncthreads_or(!done) && threadIdx.x == 0) atomicOr(status, kStatusTmaTimeout);
+}
+
+}  // namespace
+}  // namespace convtune
+
+extern "C" int ct_selftest_wait_timeout(unsigned spin_limit, void* stream) {
+  if (spin_limit == 0 || spin_limit > (1u << 24)) return CT_EINVAL;
+  int err = CT_OK;
+  unsigned* status = device_status_word(&err);
+  if (!status) return err;
+  wait_timeout_selftest_kernel<<<1, 64, 0, (cudaStream_t)stream>>>(status, spin_limit);
+  return cuda_status(cudaGetLastError());
+}

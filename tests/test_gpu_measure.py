@@ -80,3 +80,19 @@ def test_tune_at_default_clocks_small_space():
         key = "t_s" if objective == "time" else "energy_j"
         assert recs[best][key] == min(r[key] for r in valid if not math.isnan(r[key]))
     assert max_rel_err(full.cpu().numpy()[:, :512], oracle_ref(prob)) <= MAX_REL
+
+
+def test_bounded_device_wait_gives_up_and_reports():
+    # a barrier phase that nothing completes: the wait runs out after 1000
+    # polls, the kernel returns and says so in the status word
+    api.status_read(clear=True)
+    assert api.lib().ct_selftest_wait_timeout(1000, None) == api.CT_OK
+    assert api.status_read(clear=True) & 1
+    assert api.lib().ct_selftest_wait_timeout(0, None) == api.CT_EINVAL
+    # the context is still usable afterwards
+    prob = synth.conv_problem(64, 80, 9, seed=12)
+    d_in, full, d_out = to_device(prob)
+    api.conv2d_run(d_in, prob.filt, d_out, 64, 80,
+                   api.Config(32, 4, 4, 2, api.STAGE_TMA, api.FILTER_CONST, 4))
+    assert max_rel_err(full.cpu().numpy()[:, :80], oracle_ref(prob)) <= MAX_REL
+    assert api.status_read(clear=True) == 0
