@@ -82,18 +82,24 @@ def all_max(world, x):
     return float(t.item())
 
 
-def tuned_config(api, name, wl, override):
-    if override:
-        vals = [int(v) for v in override.split(",")]
-        return api.Config(*vals), "command line"
+def tuned_entry(name, wl):
     path = os.path.join(ROOT, "paper_2211_07260_gb300", "tuned_configs.json")
     key = f"{wl['h']}x{wl['w']}_k{wl['k']}"
     if os.path.exists(path):
         table = json.load(open(path))
         for dev, entries in table.get("devices", {}).items():
             if name.startswith(dev) and key in entries:
-                e = entries[key]
-                return api.Config(*e["config"]), f"tuned_configs.json ({e.get('objective')})"
+                return entries[key]
+    return None
+
+
+def tuned_config(api, name, wl, override):
+    if override:
+        vals = [int(v) for v in override.split(",")]
+        return api.Config(*vals), "command line"
+    e = tuned_entry(name, wl)
+    if e:
+        return api.Config(*e["config"]), f"tuned_configs.json ({e.get('objective')})"
     return api.Config(32, 8, 4, 2, api.STAGE_TMA, api.FILTER_CONST, 4), "built-in default"
 
 
@@ -332,6 +338,25 @@ def main():
     wall = time.perf_counter() - wall0
     step_ms = [s.elapsed_time(e) for s, e in ev]
     kernel_s = all_max(world, sum(step_ms) / 1e3)
+    # the time-optimal configuration of the same sweep, timed the same way
+    time_tuned = None
+    te = None if args.config else tuned_entry(info["name"], wl)
+    if te and te.get("time_config") and list(te["time_config"]) != list(cfg.as_tuple()):
+        tcfg = api.Config(*te["time_config"])
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                api.conv2d_run(d_in, prob.filt, d_out, wl["h"], wl["w"], tcfg, stream=stream)
+            tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for s, e in tev:
+                flush.zero_()
+                s.record(stream)
+                api.conv2d_run(d_in, prob.filt, d_out, wl["h"], wl["w"], tcfg, stream=stream)
+                e.record(stream)
+        torch.cuda.synchronize()
+        t_s = sum(s.elapsed_time(e) for s, e in tev) / 1e3 / args.steps
+        time_tuned = dict(config=list(tcfg.as_tuple()), gflops=flop / t_s / 1e9,
+                          roofline_frac=None, ms_per_step=t_s * 1e3)
     # energy: mean power over >= window of back-to-back launches (NVML energy counter)
     nan = float("nan")
     rec = dict(gflops_per_j=nan, energy_j=nan, power_w_mean=nan, power_w_median=nan,
@@ -410,6 +435,8 @@ def main():
         "clocks": ({"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                     "reasons": clocks["reasons"], "power_w_median": clocks["power_w_median"],
                     "samples_under_load": clocks["samples_under_load"]} if clocks else None),
+        "time_tuned": (dict(time_tuned, roofline_frac=time_tuned["gflops"] * 1e9 / peak)
+                       if time_tuned else None),
         "device_status_bits": status_bits,
         "timed_wall_s": wall,
         "steering": "unavailable: clock locking not permitted on this pool (tuning at default "

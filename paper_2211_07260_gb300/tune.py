@@ -72,7 +72,10 @@ def run(workload, space="basic", objective="energy", window=0.3, prefilter=0, ca
         table.setdefault("devices", {}).setdefault(name, {})[workload] = dict(
             config=list(b["cfg"]), objective=objective, space=space, window_s=window,
             prefilter=prefilter, gflops=b["gflops"], gflops_per_j=b["gflops_per_j"],
-            clocks="default")
+            clocks="default", time_config=list(summary["time_best"]["cfg"])
+            if "time_best" in summary else list(recs[tb]["cfg"]),
+            time_gflops=summary["time_best"]["gflops"] if "time_best" in summary
+            else recs[tb]["gflops"])
         with open(out, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
             f.write("\n")
