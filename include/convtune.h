@@ -127,8 +127,11 @@ int ct_conv2d_run(const ct_problem* p, const ct_config* c, void* stream);
  * The same correlation on HOST buffers (in: out_h+fh-1 rows of in_pitch
  * floats; out: out_h rows of out_pitch floats).  The library copies the
  * input to internal device buffers, runs the kernel and copies the result
- * back, all on `stream`, and returns after the stream has synchronised.
- * Pinned host memory gives the fastest copies; pageable memory works.
+ * back, and returns when the result is in `out`.  Work starts after the
+ * caller's earlier work on `stream`; large problems are split into row bands
+ * whose input copies, kernels and output copies overlap on library streams
+ * (results are identical to one launch).  Pinned host memory gives the
+ * fastest, overlapping copies; pageable memory works.
  */
 int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
                        float* out_host, long out_pitch, int out_h, int out_w,

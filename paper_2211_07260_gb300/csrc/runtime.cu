@@ -13,6 +13,7 @@
 #include <string>
 #include <tuple>
 #include <utility>
+#include <vector>
 
 #include "runtime.h"
 
@@ -30,7 +31,13 @@ struct DeviceState {
   size_t din_bytes = 0;
   float* dout = nullptr;
   size_t dout_bytes = 0;
+  // streams and events of the pipelined host-buffer entry point
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  cudaEvent_t ev_start = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_k;
 };
+
+constexpr int kHostMaxBands = 16;
 
 std::mutex g_mu;        // guards g_dev
 std::mutex g_host_mu;   // serialises the host-buffer entry point
@@ -394,9 +401,11 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
   int err = CT_OK;
   DeviceState* st = current_state(nullptr, &err);
   if (!st) return err;
-  const size_t in_bytes = sizeof(float) * (size_t)(out_h + fh - 1) * (size_t)in_pitch;
-  const size_t out_bytes = sizeof(float) * (size_t)out_h * (size_t)out_pitch;
-  cudaStream_t s = (cudaStream_t)stream;
+  const int in_h = out_h + fh - 1;
+  const size_t in_row = sizeof(float) * (size_t)in_pitch;
+  const size_t out_row = sizeof(float) * (size_t)out_pitch;
+  const size_t in_bytes = in_row * (size_t)in_h;
+  const size_t out_bytes = out_row * (size_t)out_h;
   cudaError_t e;
   if (st->din_bytes < in_bytes) {
     if (st->din) cudaFree(st->din);
@@ -412,26 +421,72 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
     if ((e = cudaMalloc(&st->dout, out_bytes)) != cudaSuccess) return cuda_status(e);
     st->dout_bytes = out_bytes;
   }
-  if ((e = cudaMemcpyAsync(st->din, in_host, in_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_status(e);
-  ct_problem p;
-  p.in = st->din;
-  p.in_pitch = in_pitch;
-  p.filt = filt;
-  p.fh = fh;
-  p.fw = fw;
-  p.out = st->dout;
-  p.out_pitch = out_pitch;
-  p.out_h = out_h;
-  p.out_w = out_w;
-  int rc = ct_conv2d_run(&p, c, stream);
-  if (rc != CT_OK) {
-    cudaStreamSynchronize(s);
-    return rc;
+  if (!st->s_in) {
+    if ((e = cudaStreamCreateWithFlags(&st->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&st->s_comp, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&st->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&st->ev_start, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_status(e);
+    st->ev_in.resize(kHostMaxBands);
+    st->ev_k.resize(kHostMaxBands);
+    for (int b = 0; b < kHostMaxBands; ++b)
+      if ((e = cudaEventCreateWithFlags(&st->ev_in[b], cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&st->ev_k[b], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_status(e);
   }
-  if ((e = cudaMemcpyAsync(out_host, st->dout, out_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cuda_status(e);
-  return cuda_status(cudaStreamSynchronize(s));
+  // Row bands: the input rows of band b travel in while band b-1 computes and
+  // band b-2's outputs travel back (host <-> device copies run both ways at
+  // once).  Input chunk b holds only the rows band b needs beyond the earlier
+  // chunks; each output is computed exactly as in one launch.
+  const int bands = std::max(1, std::min(kHostMaxBands, out_h / 256));
+  const int rows = (out_h + bands - 1) / bands;
+  int rc = CT_OK;
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(st->s_in);
+    cudaStreamSynchronize(st->s_comp);
+    cudaStreamSynchronize(st->s_out);
+    return code;
+  };
+  // start after the caller's earlier work on `stream`
+  if ((e = cudaEventRecord(st->ev_start, (cudaStream_t)stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st->s_in, st->ev_start, 0)) != cudaSuccess)
+    return fail(cuda_status(e));
+  int in_done = 0;  // input rows already sent
+  for (int b = 0; b < bands; ++b) {
+    const int y0 = b * rows;
+    const int rb = std::min(rows, out_h - y0);
+    if (rb <= 0) break;
+    const int need = y0 + rb + fh - 1;  // input rows band b reads
+    if (need > in_done) {
+      e = cudaMemcpyAsync(reinterpret_cast<char*>(st->din) + in_row * in_done,
+                          reinterpret_cast<const char*>(in_host) + in_row * in_done,
+                          in_row * (size_t)(need - in_done), cudaMemcpyHostToDevice, st->s_in);
+      if (e != cudaSuccess) return fail(cuda_status(e));
+      in_done = need;
+    }
+    if ((e = cudaEventRecord(st->ev_in[b], st->s_in)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st->s_comp, st->ev_in[b], 0)) != cudaSuccess)
+      return fail(cuda_status(e));
+    ct_problem p;
+    p.in = st->din + (size_t)y0 * in_pitch;
+    p.in_pitch = in_pitch;
+    p.filt = filt;
+    p.fh = fh;
+    p.fw = fw;
+    p.out = st->dout + (size_t)y0 * out_pitch;
+    p.out_pitch = out_pitch;
+    p.out_h = rb;
+    p.out_w = out_w;
+    if ((rc = ct_conv2d_run(&p, c, st->s_comp)) != CT_OK) return fail(rc);
+    if ((e = cudaEventRecord(st->ev_k[b], st->s_comp)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st->s_out, st->ev_k[b], 0)) != cudaSuccess)
+      return fail(cuda_status(e));
+    e = cudaMemcpyAsync(reinterpret_cast<char*>(out_host) + out_row * y0,
+                        reinterpret_cast<const char*>(st->dout) + out_row * y0,
+                        out_row * (size_t)rb, cudaMemcpyDeviceToHost, st->s_out);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+  }
+  return cuda_status(cudaStreamSynchronize(st->s_out));
 }
 
 int ct_status_read(unsigned* bits, int clear) {

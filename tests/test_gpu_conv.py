@@ -168,8 +168,11 @@ def test_grid_limit_is_reported():
     assert rc == api.CT_OK
 
 
-def test_host_entry_point_matches_device_run():
-    prob = synth.conv_problem(300, 257, 7, seed=3)
+@pytest.mark.parametrize("shape", [(300, 257, 7), (1100, 300, 9), (4100, 96, 17)])
+def test_host_entry_point_matches_device_run(shape):
+    # several row bands for the larger shapes (copies overlap the kernels)
+    h, w, k = shape
+    prob = synth.conv_problem(h, w, k, seed=3)
     cfg = api.Config(32, 4, 4, 2, api.STAGE_SMEM, api.FILTER_CONST, 4)
     d_in, full, d_out = to_device(prob)
     run(prob, cfg, d_in, d_out)
@@ -177,6 +180,12 @@ def test_host_entry_point_matches_device_run():
     host_out = np.full((prob.out_h, dev.shape[1]), -1.0, np.float32)
     api.conv2d_run_host(prob.inp, prob.filt, host_out, prob.out_h, prob.out_w, cfg)
     assert np.array_equal(host_out[:, :prob.out_w], dev[:, :prob.out_w])
+    # pinned buffers (asynchronous, overlapping copies) give the same bits
+    pin_in = torch.from_numpy(prob.inp).pin_memory().numpy()
+    pin_out = torch.full(host_out.shape, -1.0).pin_memory().numpy()
+    api.conv2d_run_host(pin_in, prob.filt, pin_out, prob.out_h, prob.out_w, cfg)
+    assert np.array_equal(pin_out, host_out)
+    assert max_rel_err(host_out[:, :prob.out_w], oracle_ref(prob)) <= MAX_REL
 
 
 @pytest.mark.parametrize("which", ["1024x1024_k7", "4096x4096_k17"])
