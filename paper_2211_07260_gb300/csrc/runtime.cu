@@ -481,9 +481,16 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
     if ((e = cudaEventRecord(st->ev_k[b], st->s_comp)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(st->s_out, st->ev_k[b], 0)) != cudaSuccess)
       return fail(cuda_status(e));
-    e = cudaMemcpyAsync(reinterpret_cast<char*>(out_host) + out_row * y0,
-                        reinterpret_cast<const char*>(st->dout) + out_row * y0,
-                        out_row * (size_t)rb, cudaMemcpyDeviceToHost, st->s_out);
+    // the caller's padding columns (out_w .. out_pitch) are left untouched
+    if (out_pitch == out_w)
+      e = cudaMemcpyAsync(reinterpret_cast<char*>(out_host) + out_row * y0,
+                          reinterpret_cast<const char*>(st->dout) + out_row * y0,
+                          out_row * (size_t)rb, cudaMemcpyDeviceToHost, st->s_out);
+    else
+      e = cudaMemcpy2DAsync(reinterpret_cast<char*>(out_host) + out_row * y0, out_row,
+                            reinterpret_cast<const char*>(st->dout) + out_row * y0, out_row,
+                            sizeof(float) * (size_t)out_w, rb, cudaMemcpyDeviceToHost,
+                            st->s_out);
     if (e != cudaSuccess) return fail(cuda_status(e));
   }
   return cuda_status(cudaStreamSynchronize(st->s_out));

@@ -185,6 +185,7 @@ def test_host_entry_point_matches_device_run(shape):
     pin_out = torch.full(host_out.shape, -1.0).pin_memory().numpy()
     api.conv2d_run_host(pin_in, prob.filt, pin_out, prob.out_h, prob.out_w, cfg)
     assert np.array_equal(pin_out, host_out)
+    assert np.all(host_out[:, prob.out_w:] == -1.0)  # padding columns untouched
     assert max_rel_err(host_out[:, :prob.out_w], oracle_ref(prob)) <= MAX_REL
 
 
