@@ -68,10 +68,28 @@ __device__ __forceinline__ void batch_tile(const BatchImage& im, int t, float* s
 
   float acc[TY][TX];
   const float* sbase = tile + (ly * TY) * st.smem_pitch + lx * TX;
-  accumulate_tile<K, TX, TY>(
-      acc,
-      [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
-      [&](int j, int i) -> float { return sfilt[j * KP + i]; });
+  // large bodies take the ring form, as in the single-image kernel (this
+  // kernel holds one body per filter side and tile height, so its code size
+  // matters even more)
+  if constexpr (TX * TY * K * K > 2500) {
+    accumulate_tile_ring<K, TX, TY>(
+        acc, [&](int r) { return sbase + r * st.smem_pitch; },
+        [&](int j, float(&w)[KP]) {
+#pragma unroll
+          for (int i = 0; i < KP; i += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(sfilt + j * KP + i);
+            w[i] = q.x;
+            w[i + 1] = q.y;
+            w[i + 2] = q.z;
+            w[i + 3] = q.w;
+          }
+        });
+  } else {
+    accumulate_tile<K, TX, TY>(
+        acc,
+        [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
+        [&](int j, int i) -> float { return sfilt[j * KP + i]; });
+  }
   const int x0 = gx0 + lx * TX, y0 = gy0 + ly * TY;
 #pragma unroll
   for (int r = 0; r < TY; ++r) {
