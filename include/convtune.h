@@ -128,14 +128,39 @@ int ct_conv2d_run(const ct_problem* p, const ct_config* c, void* stream);
  * floats; out: out_h rows of out_pitch floats).  The library copies the
  * input to internal device buffers, runs the kernel and copies the result
  * back, and returns when the result is in `out`.  Work starts after the
- * caller's earlier work on `stream`; large problems are split into row bands
- * whose input copies, kernels and output copies overlap on library streams
- * (results are identical to one launch).  Pinned host memory gives the
+ * caller's earlier work on `stream`; problems of 512 rows or more are split
+ * into row bands (ct_conv2d_host_bands_default) whose input copies, kernels
+ * and output copies overlap on library streams (results are identical to
+ * one launch).  Pinned host memory gives the
  * fastest, overlapping copies; pageable memory works.
  */
 int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
                        float* out_host, long out_pitch, int out_h, int out_w,
                        const ct_config* c, void* stream);
+
+/*
+ * ct_conv2d_run_host with the row bands given by the caller: band b covers
+ * band_rows[b] output rows, in order from row 0 (band_rows[b] >= 1, their sum
+ * == out_h, 1 <= n_bands <= 64; otherwise CT_EINVAL).  Each band is one
+ * kernel launch whose input copy overlaps the previous band's kernel and the
+ * output copy of the one before; results are identical to one launch for any
+ * split.  ct_conv2d_run_host uses the split ct_conv2d_host_bands_default
+ * returns.  (Pipelining of host copies: not in the paper, whose kernels read
+ * device-resident inputs.)
+ */
+int ct_conv2d_run_host_bands(const float* in_host, long in_pitch, const float* filt, int fh,
+                             int fw, float* out_host, long out_pitch, int out_h, int out_w,
+                             const ct_config* c, const int* band_rows, int n_bands,
+                             void* stream);
+
+/*
+ * The default split of out_h >= 1 output rows: an even split (sizes differ
+ * by at most one row) into max(min(out_h / 256, 8), ceil(out_h / 512))
+ * bands, at least 1 and at most 64.  Writes up to `cap` band sizes and the
+ * count to *n_bands; CT_ENOMEM if cap is too small (the count is still
+ * written), CT_EINVAL for out_h < 1 or a NULL n_bands.
+ */
+int ct_conv2d_host_bands_default(int out_h, int* band_rows, int cap, int* n_bands);
 
 /*
  * Device status word shared by the library's kernels (bit 0: a TMA tile wait

@@ -161,6 +161,9 @@ _SIGS = {
     "ct_conv2d_run": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ct_conv2d_run_host": (c_int, [c_void_p, c_long, c_void_p, c_int, c_int, c_void_p, c_long,
                                    c_int, c_int, c_void_p, c_void_p]),
+    "ct_conv2d_run_host_bands": (c_int, [c_void_p, c_long, c_void_p, c_int, c_int, c_void_p, c_long,
+                                         c_int, c_int, c_void_p, c_void_p, c_int, c_void_p]),
+    "ct_conv2d_host_bands_default": (c_int, [c_int, c_void_p, c_int, c_void_p]),
     "ct_status_read": (c_int, [ctypes.POINTER(ctypes.c_uint), c_int]),
     "ct_device_info_get": (c_int, [c_void_p]),
     "ct_set_platform_ops": (c_int, [c_void_p]),
@@ -315,18 +318,36 @@ def conv2d_run(inp, filt, out, out_h, out_w, cfg: Config, stream=None, in_pitch=
 
 
 def conv2d_run_host(inp: np.ndarray, filt, out: np.ndarray, out_h: int, out_w: int, cfg: Config,
-                    stream=None):
-    """The correlation on host arrays (copies in and out inside the call)."""
+                    stream=None, bands=None):
+    """The correlation on host arrays (copies in and out inside the call).
+
+    ``bands``: optional output-row counts of the pipelined row bands (their
+    sum is out_h); None takes the library's default split."""
     if inp.dtype != np.float32 or out.dtype != np.float32:
         raise TypeError("float32 arrays required")
     if not (inp.flags.c_contiguous and out.flags.c_contiguous):
         raise ValueError("contiguous arrays required")
     f = _taps(filt)
     c = cfg.to_c()
-    _check(lib().ct_conv2d_run_host(inp.ctypes.data, inp.shape[1], f.ctypes.data, f.shape[0],
-                                    f.shape[1], out.ctypes.data, out.shape[1], int(out_h),
-                                    int(out_w), ctypes.byref(c), c_void_p(stream_handle(stream))),
-           "ct_conv2d_run_host")
+    args = (inp.ctypes.data, inp.shape[1], f.ctypes.data, f.shape[0], f.shape[1],
+            out.ctypes.data, out.shape[1], int(out_h), int(out_w), ctypes.byref(c))
+    if bands is None:
+        _check(lib().ct_conv2d_run_host(*args, c_void_p(stream_handle(stream))),
+               "ct_conv2d_run_host")
+        return
+    rows = np.ascontiguousarray(bands, dtype=np.int32)
+    _check(lib().ct_conv2d_run_host_bands(*args, rows.ctypes.data, int(rows.size),
+                                          c_void_p(stream_handle(stream))),
+           "ct_conv2d_run_host_bands")
+
+
+def host_bands_default(out_h: int) -> list:
+    """The library's default row-band split for out_h output rows."""
+    buf = np.zeros(64, np.int32)
+    n = c_int(0)
+    _check(lib().ct_conv2d_host_bands_default(int(out_h), buf.ctypes.data, 64, ctypes.byref(n)),
+           "ct_conv2d_host_bands_default")
+    return buf[:n.value].tolist()
 
 
 def status_read(clear: bool = False) -> int:

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <set>
+#include <vector>
 #include <string>
 #include <tuple>
 #include <utility>
@@ -37,7 +38,7 @@ struct DeviceState {
   std::vector<cudaEvent_t> ev_in, ev_k;
 };
 
-constexpr int kHostMaxBands = 16;
+constexpr int kHostMaxBands = 64;
 
 std::mutex g_mu;        // guards g_dev
 std::mutex g_host_mu;   // serialises the host-buffer entry point
@@ -389,14 +390,29 @@ int ct_conv2d_run(const ct_problem* p, const ct_config* c, void* stream) {
   return launch_plan(plan, (cudaStream_t)stream);
 }
 
-int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
-                       float* out_host, long out_pitch, int out_h, int out_w, const ct_config* c,
-                       void* stream) {
-  if (!c || !filt) return CT_EINVAL;
-  if (out_h < 0 || out_w < 0 || fh < 1 || fw < 1) return CT_EINVAL;
-  if (out_h == 0 || out_w == 0) return CT_OK;
-  if (!in_host || !out_host) return CT_EINVAL;
-  if (in_pitch < (long)out_w + fw - 1 || out_pitch < out_w) return CT_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// Default row bands of the host-buffer entry point: an even split into
+// n = max(min(out_h / 256, 8), ceil(out_h / 512)) bands (at least 1, at most
+// kHostMaxBands).  Each band costs a few microseconds of copy and launch
+// set-up, and the first input copy and the last output copy overlap nothing,
+// so bands of a few hundred rows balance the two; on GB300, 4096 rows ran
+// fastest as 8 bands (4, 16 and 32 bands, and bands ramping from 64 rows at
+// both ends, were slower).
+std::vector<int> default_host_bands(int out_h) {
+  const long long h = out_h;
+  long long n = std::max(std::min(h / 256, 8LL), (h + 511) / 512);
+  n = std::max(1LL, std::min(n, (long long)kHostMaxBands));
+  std::vector<int> rows;
+  for (long long b = 0; b < n; ++b) rows.push_back((int)(h / n + (b < h % n ? 1 : 0)));
+  return rows;
+}
+
+int run_host_bands(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
+                   float* out_host, long out_pitch, int out_h, int out_w, const ct_config* c,
+                   const int* band_rows, int n_bands, void* stream) {
   std::lock_guard<std::mutex> lk(g_host_mu);
   int err = CT_OK;
   DeviceState* st = current_state(nullptr, &err);
@@ -434,12 +450,12 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
           (e = cudaEventCreateWithFlags(&st->ev_k[b], cudaEventDisableTiming)) != cudaSuccess)
         return cuda_status(e);
   }
-  // Row bands: the input rows of band b travel in while band b-1 computes and
-  // band b-2's outputs travel back (host <-> device copies run both ways at
+  // The input rows of band b travel in while band b-1 computes and band
+  // b-2's outputs travel back (host <-> device copies run both ways at
   // once).  Input chunk b holds only the rows band b needs beyond the earlier
-  // chunks; each output is computed exactly as in one launch.
-  const int bands = std::max(1, std::min(kHostMaxBands, out_h / 256));
-  const int rows = (out_h + bands - 1) / bands;
+  // chunks; each output is computed exactly as in one launch.  (One stream
+  // per stage: spreading the bands over two streams per stage, so that two
+  // copies of one direction run at once, measured slower.)
   int rc = CT_OK;
   auto fail = [&](int code) {
     cudaStreamSynchronize(st->s_in);
@@ -452,18 +468,15 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
       (e = cudaStreamWaitEvent(st->s_in, st->ev_start, 0)) != cudaSuccess)
     return fail(cuda_status(e));
   int in_done = 0;  // input rows already sent
-  for (int b = 0; b < bands; ++b) {
-    const int y0 = b * rows;
-    const int rb = std::min(rows, out_h - y0);
-    if (rb <= 0) break;
-    const int need = y0 + rb + fh - 1;  // input rows band b reads
-    if (need > in_done) {
-      e = cudaMemcpyAsync(reinterpret_cast<char*>(st->din) + in_row * in_done,
-                          reinterpret_cast<const char*>(in_host) + in_row * in_done,
-                          in_row * (size_t)(need - in_done), cudaMemcpyHostToDevice, st->s_in);
-      if (e != cudaSuccess) return fail(cuda_status(e));
-      in_done = need;
-    }
+  int y0 = 0;
+  for (int b = 0; b < n_bands; ++b) {
+    const int rb = band_rows[b];
+    const int need = y0 + rb + fh - 1;  // input rows band b reads (> in_done: rb >= 1)
+    e = cudaMemcpyAsync(reinterpret_cast<char*>(st->din) + in_row * in_done,
+                        reinterpret_cast<const char*>(in_host) + in_row * in_done,
+                        in_row * (size_t)(need - in_done), cudaMemcpyHostToDevice, st->s_in);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    in_done = need;
     if ((e = cudaEventRecord(st->ev_in[b], st->s_in)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(st->s_comp, st->ev_in[b], 0)) != cudaSuccess)
       return fail(cuda_status(e));
@@ -492,8 +505,60 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
                             sizeof(float) * (size_t)out_w, rb, cudaMemcpyDeviceToHost,
                             st->s_out);
     if (e != cudaSuccess) return fail(cuda_status(e));
+    y0 += rb;
   }
   return cuda_status(cudaStreamSynchronize(st->s_out));
+}
+
+int host_args_check(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
+                    float* out_host, long out_pitch, int out_h, int out_w, const ct_config* c) {
+  if (!c || !filt) return CT_EINVAL;
+  if (out_h < 0 || out_w < 0 || fh < 1 || fw < 1) return CT_EINVAL;
+  if (out_h == 0 || out_w == 0) return CT_OK;
+  if (!in_host || !out_host) return CT_EINVAL;
+  if (in_pitch < (long)out_w + fw - 1 || out_pitch < out_w) return CT_EINVAL;
+  return CT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
+                       float* out_host, long out_pitch, int out_h, int out_w, const ct_config* c,
+                       void* stream) {
+  int rc = host_args_check(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c);
+  if (rc != CT_OK || out_h == 0 || out_w == 0) return rc;
+  const std::vector<int> rows = default_host_bands(out_h);
+  return run_host_bands(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c,
+                        rows.data(), (int)rows.size(), stream);
+}
+
+int ct_conv2d_run_host_bands(const float* in_host, long in_pitch, const float* filt, int fh,
+                             int fw, float* out_host, long out_pitch, int out_h, int out_w,
+                             const ct_config* c, const int* band_rows, int n_bands,
+                             void* stream) {
+  int rc = host_args_check(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c);
+  if (rc != CT_OK) return rc;
+  if (!band_rows || n_bands < 1 || n_bands > kHostMaxBands) return CT_EINVAL;
+  long long total = 0;
+  for (int b = 0; b < n_bands; ++b) {
+    if (band_rows[b] < 1) return CT_EINVAL;
+    total += band_rows[b];
+  }
+  if (total != out_h) return CT_EINVAL;
+  if (out_w == 0) return CT_OK;
+  return run_host_bands(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c,
+                        band_rows, n_bands, stream);
+}
+
+int ct_conv2d_host_bands_default(int out_h, int* band_rows, int cap, int* n_bands) {
+  if (out_h < 1 || !n_bands) return CT_EINVAL;
+  const std::vector<int> rows = default_host_bands(out_h);
+  *n_bands = (int)rows.size();
+  if (cap < (int)rows.size() || !band_rows) return CT_ENOMEM;
+  for (size_t b = 0; b < rows.size(); ++b) band_rows[b] = rows[b];
+  return CT_OK;
 }
 
 int ct_status_read(unsigned* bits, int clear) {

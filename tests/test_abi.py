@@ -61,3 +61,38 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     bad = api.Config(block_x=48).to_c()
     p = api.CtProblem(16, 12, ctypes.addressof(taps), 3, 3, 32, 8, 4, 8)
     assert lib.ct_conv2d_check(ctypes.byref(p), ctypes.byref(bad), None, 0) == api.CT_ECONFIG
+
+
+def test_default_host_band_split(lib):
+    # host logic of the pipelined host-buffer entry point: an even split into
+    # max(min(h // 256, 8), ceil(h / 512)) bands, 1..64 of them, covering
+    # every row once
+    assert api.host_bands_default(1) == [1]
+    assert api.host_bands_default(511) == [511]
+    assert api.host_bands_default(512) == [256, 256]
+    assert api.host_bands_default(1024) == [256] * 4
+    assert api.host_bands_default(4096) == [512] * 8
+    assert api.host_bands_default(8192) == [512] * 16
+    assert api.host_bands_default(1000) == [334, 333, 333]
+    for h in (513, 4097, 32767, 70000, 2**31 - 1):
+        b = api.host_bands_default(h)
+        n = max(min(h // 256, 8), -(-h // 512))
+        assert len(b) == min(n, 64) and sum(b) == h and max(b) - min(b) <= 1, h
+    n = ctypes.c_int(0)
+    assert lib.ct_conv2d_host_bands_default(0, None, 0, ctypes.byref(n)) == api.CT_EINVAL
+    assert lib.ct_conv2d_host_bands_default(4096, None, 0, ctypes.byref(n)) == api.CT_ENOMEM
+    assert n.value == 8
+
+
+def test_explicit_band_split_is_checked_on_the_host(lib):
+    taps = (ctypes.c_float * 9)()
+    buf_in = (ctypes.c_float * (10 * 10))()
+    buf_out = (ctypes.c_float * (8 * 8))()
+    c = api.Config().to_c()
+
+    def run(rows):
+        arr = (ctypes.c_int * len(rows))(*rows)
+        return lib.ct_conv2d_run_host_bands(buf_in, 10, taps, 3, 3, buf_out, 8, 8, 8,
+                                            ctypes.byref(c), arr, len(rows), None)
+    for bad in ([8, 0], [4, 3], [4, 5], [1] * 65, [-1, 9]):
+        assert run(bad) == api.CT_EINVAL, bad

@@ -189,6 +189,26 @@ def test_host_entry_point_matches_device_run(shape):
     assert max_rel_err(host_out[:, :prob.out_w], oracle_ref(prob)) <= MAX_REL
 
 
+def test_host_entry_point_explicit_bands():
+    # any split of the rows gives the same bits as one launch; bad splits are
+    # rejected before any copy
+    prob = synth.conv_problem(700, 128, 5, seed=4)
+    cfg = api.Config(32, 4, 4, 2, api.STAGE_TMA, api.FILTER_CONST, 4)
+    ref = np.empty((700, 128), np.float32)
+    api.conv2d_run_host(prob.inp, prob.filt, ref, 700, 128, cfg, bands=[700])
+    assert max_rel_err(ref, oracle_ref(prob)) <= MAX_REL
+    for split in ([1, 2, 697], [350, 350], [64] * 10 + [60], [699, 1], [11] * 63 + [7]):
+        out = np.full((700, 128), -1.0, np.float32)
+        api.conv2d_run_host(prob.inp, prob.filt, out, 700, 128, cfg, bands=split)
+        assert np.array_equal(out, ref), split
+    out = np.full((700, 128), -1.0, np.float32)
+    for bad in ([700, 0], [350, 349], [350, 351], [10] * 70, [-1, 701]):
+        with pytest.raises(api.ConvTuneError) as e:
+            api.conv2d_run_host(prob.inp, prob.filt, out, 700, 128, cfg, bands=bad)
+        assert e.value.status == api.CT_EINVAL
+    assert np.all(out == -1.0)
+
+
 @pytest.mark.parametrize("which", ["1024x1024_k7", "4096x4096_k17"])
 def test_full_size_workloads(which):
     if which == "1024x1024_k7":
