@@ -70,9 +70,10 @@ __device__ __forceinline__ void batch_tile(const BatchImage& im, int t, float* s
   const float* sbase = tile + (ly * TY) * st.smem_pitch + lx * TX;
   // large bodies take the ring form, as in the single-image kernel (this
   // kernel holds one body per filter side and tile height, so its code size
-  // matters even more)
+  // matters even more); taps come from shared memory, so the loop keeps its
+  // bounds tests (the peeled form needs 128 registers and a stack frame here)
   if constexpr (TX * TY * K * K > 2500) {
-    accumulate_tile_ring<K, TX, TY>(
+    accumulate_tile_ring<K, TX, TY, false>(
         acc, [&](int r) { return sbase + r * st.smem_pitch; },
         [&](int j, float(&w)[KP]) {
 #pragma unroll

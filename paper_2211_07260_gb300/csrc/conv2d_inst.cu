@@ -51,7 +51,8 @@ const void* CT_CAT(pick_k, CT_K)(int tx, int ty, bool staged, bool filt_smem) {
 cudaError_t CT_CAT(launch_k, CT_K)(const ConvLaunch& L, cudaStream_t s) {
   const void* fn = CT_CAT(pick_k, CT_K)(L.tx, L.ty, L.staging != kStageDirect, L.filt_smem != 0);
   if (!fn) return cudaErrorInvalidValue;
-  ConvArgs<K * K> a;
+  constexpr int KP = tap_row_pad(K);
+  ConvArgs<K * KP> a;
   memset(&a, 0, sizeof(a));
   if (L.tmap) a.tmap = *L.tmap;
   a.in = L.in;
@@ -70,7 +71,7 @@ cudaError_t CT_CAT(launch_k, CT_K)(const ConvLaunch& L, cudaStream_t s) {
   a.smem_pitch = L.smem_pitch;
   a.tile_w = L.tile_w;
   a.tile_h = L.tile_h;
-  memcpy(a.w, L.taps, sizeof(float) * K * K);
+  for (int j = 0; j < K; ++j) memcpy(a.w + j * KP, L.taps + j * K, sizeof(float) * K);
   const dim3 block(L.bx, L.by);
   const dim3 grid((L.out_w + L.bx * L.tx - 1) / (L.bx * L.tx),
                   (L.out_h + L.by * L.ty - 1) / (L.by * L.ty));

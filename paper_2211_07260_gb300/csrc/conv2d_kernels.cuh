@@ -48,8 +48,14 @@ struct alignas(64) ConvArgs {
   int staging;               // kStageDirect / kStageSmem / kStageTma
   int smem_pitch;            // floats per shared-memory tile row
   int tile_w, tile_h;        // staged tile (floats); tile_w % 4 == 0
-  float w[NTAPS];            // taps, row-major fh x fw
+  // taps: the specialised kernels keep K rows of KP = round_up(K, 4) floats
+  // (zero padded; a tap row is whole 16-byte words), the generic kernel
+  // fh rows of fw floats
+  alignas(16) float w[NTAPS];
 };
+
+// Floats per tap row of the specialised K x K kernels.
+__host__ __device__ constexpr int tap_row_pad(int k) { return (k + 3) / 4 * 4; }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -312,7 +318,7 @@ __device__ __forceinline__ void accumulate_tile(float (&acc)[TY][TX], FetchRow&&
 // result.  ROWP(r) points at input row r (shared memory, 16-byte aligned);
 // TAPROW(j, w) fills w[0 .. K-1] with filter row j.
 // ----------------------------------------------------------------------------
-template <int K, int TX, int TY, class RowPtr, class TapRow>
+template <int K, int TX, int TY, bool PEEL, class RowPtr, class TapRow>
 __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPtr&& rowp,
                                                      TapRow&& taprow) {
   constexpr int N = TX + K - 1;
@@ -324,25 +330,60 @@ __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPt
     for (int x = 0; x < TX; ++x) acc[t][x] = 0.0f;
     fetch_row_smem<K, TX>(ring[t], rowp(t));
   }
-  constexpr int NB = (K + TY - 1) / TY;
-#pragma unroll 1
-  for (int jb = 0; jb < NB; ++jb) {
+  // one filter row j (jj = j % TY, a compile-time ring position): output
+  // row t reads input row j + t, held in slot (t + jj) % TY
+  auto row_taps = [&](int jj, const float(&w)[KP]) {
 #pragma unroll
-    for (int jj = 0; jj < TY; ++jj) {
-      const int j = jb * TY + jj;
-      if (j < K) {
+    for (int t = 0; t < TY; ++t)
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int x = 0; x < TX; ++x)
+          acc[t][x] = fmaf(ring[(t + jj) % TY][x + i], w[i], acc[t][x]);
+  };
+  if constexpr (PEEL) {
+    // K / TY whole blocks of TY filter rows in a loop, the K % TY rows left
+    // after it unrolled (no per-row bounds tests in the loop)
+    constexpr int NBF = K / TY, REM = K % TY;
+#pragma unroll 1
+    for (int jb = 0; jb < NBF; ++jb) {
+      // no loads move across blocks (prefetched taps would hold registers
+      // throughout the loop)
+      asm volatile("" ::: "memory");
+#pragma unroll
+      for (int jj = 0; jj < TY; ++jj) {
+        const int j = jb * TY + jj;
         float w[KP];
         taprow(j, w);
-#pragma unroll
-        for (int t = 0; t < TY; ++t)
-#pragma unroll
-          for (int i = 0; i < K; ++i)
-#pragma unroll
-            for (int x = 0; x < TX; ++x)
-              acc[t][x] = fmaf(ring[(t + jj) % TY][x + i], w[i], acc[t][x]);
+        row_taps(jj, w);
         // slot jj held input row j (needed by output row 0 only); it now
         // takes row j + TY, needed from filter row j + 1 on
-        if (j + 1 < K) fetch_row_smem<K, TX>(ring[jj], rowp(TY + j));
+        if (jj + 1 < TY || REM > 0 || jb + 1 < NBF) fetch_row_smem<K, TX>(ring[jj], rowp(TY + j));
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < REM; ++jj) {
+      const int j = NBF * TY + jj;
+      float w[KP];
+      taprow(j, w);
+      row_taps(jj, w);
+      if (jj + 1 < REM) fetch_row_smem<K, TX>(ring[jj], rowp(TY + j));
+    }
+  } else {
+    // ceil(K / TY) blocks, rows past K skipped (taps read from shared
+    // memory: the peeled form above takes more registers there)
+    constexpr int NB = (K + TY - 1) / TY;
+#pragma unroll 1
+    for (int jb = 0; jb < NB; ++jb) {
+#pragma unroll
+      for (int jj = 0; jj < TY; ++jj) {
+        const int j = jb * TY + jj;
+        if (j < K) {
+          float w[KP];
+          taprow(j, w);
+          row_taps(jj, w);
+          if (j + 1 < K) fetch_row_smem<K, TX>(ring[jj], rowp(TY + j));
+        }
       }
     }
   }
@@ -356,23 +397,21 @@ __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPt
 //                        [staged tile tile_h x smem_pitch (if STAGED)]
 // ----------------------------------------------------------------------------
 template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM>
-__global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
+__global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K)> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  // tap rows padded to a multiple of 4 floats: 4 taps per broadcast LDS.128
-  constexpr int KP = (K + 3) / 4 * 4;
+  // tap rows padded to a multiple of 4 floats (in the parameters and in
+  // shared memory): 4 taps per 16-byte load
+  constexpr int KP = tap_row_pad(K);
   constexpr int kFiltFloats = FILT_SMEM ? ((K * KP + 31) / 32) * 32 : 0;
   float* sfilt = reinterpret_cast<float*>(smem_raw);
   const int bx = blockDim.x, by = blockDim.y;
 
   if constexpr (FILT_SMEM) {
-    for (int k = threadIdx.y * bx + threadIdx.x; k < K * KP; k += bx * by) {
-      const int j = k / KP, i = k - j * KP;
-      sfilt[k] = i < K ? a.w[j * K + i] : 0.0f;
-    }
+    for (int k = threadIdx.y * bx + threadIdx.x; k < K * KP; k += bx * by) sfilt[k] = a.w[k];
   }
   auto tap = [&](int j, int i) -> float {
     if constexpr (FILT_SMEM) return sfilt[j * KP + i];
-    else return a.w[j * K + i];
+    else return a.w[j * KP + i];
   };
   float acc[TY][TX];
 
@@ -410,7 +449,7 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
     // variants take the ring form (measured on GB300: 17 x 17, 4 x 4 tiles,
     // 54 -> 63 TFLOP/s; smaller bodies are faster unrolled).
     if constexpr (TX * TY * K * K > 2500) {
-      accumulate_tile_ring<K, TX, TY>(
+      accumulate_tile_ring<K, TX, TY, !FILT_SMEM>(
           acc, [&](int r) { return sbase + r * a.smem_pitch; },
           [&](int j, float(&w)[KP]) {
             if constexpr (FILT_SMEM) {
@@ -424,7 +463,7 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * K> a) {
               }
             } else {
 #pragma unroll
-              for (int i = 0; i < K; ++i) w[i] = a.w[j * K + i];
+              for (int i = 0; i < K; ++i) w[i] = a.w[j * KP + i];
             }
           });
     } else {
