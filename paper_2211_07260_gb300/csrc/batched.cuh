@@ -72,8 +72,8 @@ __device__ __forceinline__ void batch_tile(const BatchImage& im, int t, float* s
   // kernel holds one body per filter side and tile height, so its code size
   // matters even more); taps come from shared memory, so the loop keeps its
   // bounds tests (the peeled form needs 128 registers and a stack frame here)
-  if constexpr (TX * TY * K * K > 2500) {
-    accumulate_tile_ring<K, TX, TY, false>(
+  if constexpr (uses_ring(K, TX, TY)) {
+    accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
         acc, [&](int r) { return sbase + r * st.smem_pitch; },
         [&](int j, float(&w)[KP]) {
 #pragma unroll

@@ -20,36 +20,40 @@ namespace {
 constexpr int K = CT_K;
 
 template <int TX, int TY>
-const void* pick_tile(bool staged, bool filt_smem) {
-  if (staged)
-    return filt_smem ? (const void*)conv2d_kernel<K, TX, TY, true, true>
-                     : (const void*)conv2d_kernel<K, TX, TY, true, false>;
+const void* pick_tile(bool staged, bool filt_smem, bool big_cta) {
+  if (staged) {
+    if (filt_smem) return (const void*)conv2d_kernel<K, TX, TY, true, true>;
+    if constexpr (uses_ring(K, TX, TY))
+      if (big_cta) return (const void*)conv2d_kernel<K, TX, TY, true, false, true>;
+    return (const void*)conv2d_kernel<K, TX, TY, true, false>;
+  }
   return filt_smem ? (const void*)conv2d_kernel<K, TX, TY, false, true>
                    : (const void*)conv2d_kernel<K, TX, TY, false, false>;
 }
 
 template <int TX>
-const void* pick_ty(int ty, bool staged, bool filt_smem) {
+const void* pick_ty(int ty, bool staged, bool filt_smem, bool big_cta) {
   switch (ty) {
-    case 1: return pick_tile<TX, 1>(staged, filt_smem);
-    case 2: return pick_tile<TX, 2>(staged, filt_smem);
-    case 4: return pick_tile<TX, 4>(staged, filt_smem);
+    case 1: return pick_tile<TX, 1>(staged, filt_smem, big_cta);
+    case 2: return pick_tile<TX, 2>(staged, filt_smem, big_cta);
+    case 4: return pick_tile<TX, 4>(staged, filt_smem, big_cta);
     default: return nullptr;
   }
 }
 }  // namespace
 
-const void* CT_CAT(pick_k, CT_K)(int tx, int ty, bool staged, bool filt_smem) {
+const void* CT_CAT(pick_k, CT_K)(int tx, int ty, bool staged, bool filt_smem, bool big_cta) {
   switch (tx) {
-    case 1: return pick_ty<1>(ty, staged, filt_smem);
-    case 2: return pick_ty<2>(ty, staged, filt_smem);
-    case 4: return pick_ty<4>(ty, staged, filt_smem);
+    case 1: return pick_ty<1>(ty, staged, filt_smem, big_cta);
+    case 2: return pick_ty<2>(ty, staged, filt_smem, big_cta);
+    case 4: return pick_ty<4>(ty, staged, filt_smem, big_cta);
     default: return nullptr;
   }
 }
 
 cudaError_t CT_CAT(launch_k, CT_K)(const ConvLaunch& L, cudaStream_t s) {
-  const void* fn = CT_CAT(pick_k, CT_K)(L.tx, L.ty, L.staging != kStageDirect, L.filt_smem != 0);
+  const void* fn = CT_CAT(pick_k, CT_K)(L.tx, L.ty, L.staging != kStageDirect, L.filt_smem != 0,
+                                        L.bx * L.by >= kRingRemFirstThreads);
   if (!fn) return cudaErrorInvalidValue;
   constexpr int KP = tap_row_pad(K);
   ConvArgs<K * KP> a;

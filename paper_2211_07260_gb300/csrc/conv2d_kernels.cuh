@@ -57,6 +57,19 @@ struct alignas(64) ConvArgs {
 // Floats per tap row of the specialised K x K kernels.
 __host__ __device__ constexpr int tap_row_pad(int k) { return (k + 3) / 4 * 4; }
 
+// Bodies of more than ~2500 FFMAs (K*K*TX*TY) no longer fit the instruction
+// caches unrolled; they take the ring form (accumulate_tile_ring).
+__host__ __device__ constexpr bool uses_ring(int k, int tx, int ty) { return tx * ty * k * k > 2500; }
+
+// Order of the ring form's filter rows around its loop over whole blocks of
+// TY rows.  All three give the same fmaf chain per output (bitwise the same
+// result); they differ in scheduling only.  Measured on GB300 (17 x 17,
+// 4 x 4 tiles, TMA staging, constant-bank taps): CTAs of 1-4 warps ran 2-5 %
+// faster with the K % TY left-over rows after the loop, CTAs of 8 warps 2 %
+// faster with them before it; taps from shared memory keep the bounds-tested
+// loop, which takes fewer registers there.
+enum class RingSchedule { kTested, kRemLast, kRemFirst };
+
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -318,7 +331,7 @@ __device__ __forceinline__ void accumulate_tile(float (&acc)[TY][TX], FetchRow&&
 // result.  ROWP(r) points at input row r (shared memory, 16-byte aligned);
 // TAPROW(j, w) fills w[0 .. K-1] with filter row j.
 // ----------------------------------------------------------------------------
-template <int K, int TX, int TY, bool PEEL, class RowPtr, class TapRow>
+template <int K, int TX, int TY, RingSchedule SCHED, class RowPtr, class TapRow>
 __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPtr&& rowp,
                                                      TapRow&& taprow) {
   constexpr int N = TX + K - 1;
@@ -341,10 +354,10 @@ __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPt
         for (int x = 0; x < TX; ++x)
           acc[t][x] = fmaf(ring[(t + jj) % TY][x + i], w[i], acc[t][x]);
   };
-  if constexpr (PEEL) {
+  constexpr int NBF = K / TY, REM = K % TY;
+  if constexpr (SCHED == RingSchedule::kRemLast) {
     // K / TY whole blocks of TY filter rows in a loop, the K % TY rows left
     // after it unrolled (no per-row bounds tests in the loop)
-    constexpr int NBF = K / TY, REM = K % TY;
 #pragma unroll 1
     for (int jb = 0; jb < NBF; ++jb) {
       // no loads move across blocks (prefetched taps would hold registers
@@ -369,9 +382,33 @@ __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPt
       row_taps(jj, w);
       if (jj + 1 < REM) fetch_row_smem<K, TX>(ring[jj], rowp(TY + j));
     }
+  } else if constexpr (SCHED == RingSchedule::kRemFirst) {
+    // the K % TY first filter rows unrolled, then K / TY whole blocks in a
+    // loop; filter row j = REM + jb * TY + jj sits at ring position
+    // (REM + jj) % TY
+#pragma unroll
+    for (int j = 0; j < REM; ++j) {
+      float w[KP];
+      taprow(j, w);
+      row_taps(j, w);
+      fetch_row_smem<K, TX>(ring[j], rowp(TY + j));
+    }
+#pragma unroll 1
+    for (int jb = 0; jb < NBF; ++jb) {
+      asm volatile("" ::: "memory");
+#pragma unroll
+      for (int jj = 0; jj < TY; ++jj) {
+        const int j = REM + jb * TY + jj;
+        float w[KP];
+        taprow(j, w);
+        row_taps((REM + jj) % TY, w);
+        if (jj + 1 < TY || jb + 1 < NBF)
+          fetch_row_smem<K, TX>(ring[(REM + jj) % TY], rowp(TY + j));
+      }
+    }
   } else {
-    // ceil(K / TY) blocks, rows past K skipped (taps read from shared
-    // memory: the peeled form above takes more registers there)
+    // ceil(K / TY) blocks, rows past K skipped (for taps read from shared
+    // memory: the peeled forms above take more registers there)
     constexpr int NB = (K + TY - 1) / TY;
 #pragma unroll 1
     for (int jb = 0; jb < NB; ++jb) {
@@ -396,7 +433,7 @@ __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPt
 // Dynamic shared memory: [filter K x KP (if FILT_SMEM), padded to 32 floats]
 //                        [staged tile tile_h x smem_pitch (if STAGED)]
 // ----------------------------------------------------------------------------
-template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM>
+template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM, bool REM_FIRST = false>
 __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K)> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // tap rows padded to a multiple of 4 floats (in the parameters and in
@@ -448,8 +485,11 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K
     // instruction caches and warps stall on instruction fetch, so those
     // variants take the ring form (measured on GB300: 17 x 17, 4 x 4 tiles,
     // 54 -> 63 TFLOP/s; smaller bodies are faster unrolled).
-    if constexpr (TX * TY * K * K > 2500) {
-      accumulate_tile_ring<K, TX, TY, !FILT_SMEM>(
+    if constexpr (uses_ring(K, TX, TY)) {
+      constexpr RingSchedule kSched = FILT_SMEM ? RingSchedule::kTested
+                                      : REM_FIRST ? RingSchedule::kRemFirst
+                                                  : RingSchedule::kRemLast;
+      accumulate_tile_ring<K, TX, TY, kSched>(
           acc, [&](int r) { return sbase + r * a.smem_pitch; },
           [&](int j, float(&w)[KP]) {
             if constexpr (FILT_SMEM) {

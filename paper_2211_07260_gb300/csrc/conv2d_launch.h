@@ -19,6 +19,9 @@ enum : unsigned {
 constexpr int kMaxK = 17;              // largest specialised odd filter side
 constexpr int kGenericMaxTaps = 1024;  // generic kernel: fh * fw limit
 constexpr int kStageDirect = 0, kStageSmem = 1, kStageTma = 2;
+// CTAs of at least this many threads take the ring form with its left-over
+// filter rows first (RingSchedule::kRemFirst), smaller ones with them last
+constexpr int kRingRemFirstThreads = 256;
 constexpr unsigned kMbarSpinLimit = 1u << 22;
 
 struct ConvLaunch {
@@ -42,7 +45,7 @@ using KernelPicker = const void* (*)(int tx, int ty, bool staged, bool filt_smem
 using KernelLauncher = cudaError_t (*)(const ConvLaunch& L, cudaStream_t s);
 
 #define CT_DECLARE_K(K)                                                   \
-  const void* pick_k##K(int tx, int ty, bool staged, bool filt_smem);     \
+  const void* pick_k##K(int tx, int ty, bool staged, bool filt_smem, bool big_cta); \
   cudaError_t launch_k##K(const ConvLaunch& L, cudaStream_t s);
 
 CT_DECLARE_K(1)

@@ -72,17 +72,17 @@ DeviceState* current_state(int* dev_out, int* err) {
   return &st;
 }
 
-const void* pick_specialised(int k, int tx, int ty, bool staged, bool fs) {
+const void* pick_specialised(int k, int tx, int ty, bool staged, bool fs, bool big) {
   switch (k) {
-    case 1: return pick_k1(tx, ty, staged, fs);
-    case 3: return pick_k3(tx, ty, staged, fs);
-    case 5: return pick_k5(tx, ty, staged, fs);
-    case 7: return pick_k7(tx, ty, staged, fs);
-    case 9: return pick_k9(tx, ty, staged, fs);
-    case 11: return pick_k11(tx, ty, staged, fs);
-    case 13: return pick_k13(tx, ty, staged, fs);
-    case 15: return pick_k15(tx, ty, staged, fs);
-    case 17: return pick_k17(tx, ty, staged, fs);
+    case 1: return pick_k1(tx, ty, staged, fs, big);
+    case 3: return pick_k3(tx, ty, staged, fs, big);
+    case 5: return pick_k5(tx, ty, staged, fs, big);
+    case 7: return pick_k7(tx, ty, staged, fs, big);
+    case 9: return pick_k9(tx, ty, staged, fs, big);
+    case 11: return pick_k11(tx, ty, staged, fs, big);
+    case 13: return pick_k13(tx, ty, staged, fs, big);
+    case 15: return pick_k15(tx, ty, staged, fs, big);
+    case 17: return pick_k17(tx, ty, staged, fs, big);
     default: return nullptr;
   }
 }
@@ -249,7 +249,8 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
     L.filt_smem = c.filter_mem == CT_FILTER_SHARED;
     L.vw = c.vec_width;
     const bool staged = c.staging != CT_STAGE_DIRECT;
-    plan->fn = pick_specialised(K, c.tile_x, c.tile_y, staged, L.filt_smem != 0);
+    plan->fn = pick_specialised(K, c.tile_x, c.tile_y, staged, L.filt_smem != 0,
+                                c.block_x * c.block_y >= kRingRemFirstThreads);
     if (!plan->fn) return fail(CT_ECONFIG, "variant not compiled");
     plan->grid = dim3((p.out_w + c.block_x * c.tile_x - 1) / (c.block_x * c.tile_x),
                       (p.out_h + c.block_y * c.tile_y - 1) / (c.block_y * c.tile_y));
