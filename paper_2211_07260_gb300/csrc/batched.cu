@@ -11,12 +11,50 @@
 #include <vector>
 
 #include "batched.cuh"
+#include "batched_internal.h"
 #include "measure.h"
 #include "platform.h"
 #include "runtime.h"
 
 namespace convtune {
 
+template <int KK>
+__device__ __forceinline__ void run_tile_k(const BatchImage& im, int t, float* smem) {
+  if (im.ty == 1) batch_tile<KK, 1>(im, t, smem);
+  else if (im.ty == 2) batch_tile<KK, 2>(im, t, smem);
+  else batch_tile<KK, 4>(im, t, smem);
+}
+
+// One tile of a class-CLS image; a filter side outside the class (a table
+// the host did not split correctly) only raises the status bit.
+template <int CLS>
+__device__ __forceinline__ void run_tile(const BatchImage& im, int t, float* smem,
+                                         unsigned* status) {
+  switch (im.k) {
+#define CT_BATCH_CASE(KK)                                                        \
+  case KK:                                                                       \
+    if constexpr (batch_class_of(KK) == CLS) {                                   \
+      run_tile_k<KK>(im, t, smem);                                               \
+      return;                                                                    \
+    }                                                                            \
+    break;
+    CT_BATCH_CASE(1)
+    CT_BATCH_CASE(3)
+    CT_BATCH_CASE(5)
+    CT_BATCH_CASE(7)
+    CT_BATCH_CASE(9)
+    CT_BATCH_CASE(11)
+    CT_BATCH_CASE(13)
+    CT_BATCH_CASE(15)
+    CT_BATCH_CASE(17)
+#undef CT_BATCH_CASE
+    default:
+      break;
+  }
+  if (threadIdx.x == 0) atomicOr(status, kStatusBadItem);
+}
+
+template <int CLS>
 __global__ void __launch_bounds__(kBatchThreads) batched_conv_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* smem = reinterpret_cast<float*>(smem_raw);
@@ -27,11 +65,12 @@ __global__ void __launch_bounds__(kBatchThreads) batched_conv_kernel(const Batch
       const long long w = (long long)atomicAdd(a.counter, 1u);
       int img = -1;
       if (w < a.n_items) {
-        // last image whose first item is <= w
+        // last image whose first item is <= the table item
+        const long long gw = a.item_base + w;
         int lo = 0, hi = a.n_images - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) / 2;
-          if (a.images[mid].first_item <= w) lo = mid;
+          if (a.images[mid].first_item <= gw) lo = mid;
           else hi = mid - 1;
         }
         img = lo;
@@ -45,33 +84,20 @@ __global__ void __launch_bounds__(kBatchThreads) batched_conv_kernel(const Batch
     __syncthreads();  // s_item / s_img are rewritten only after this point
     if (w >= a.n_items) break;
     const BatchImage& im = a.images[img];
-    const long long tl = w - im.first_item;
+    const long long tl = a.item_base + w - im.first_item;
     if (tl < 0 || tl >= (long long)im.tiles_x * im.tiles_y) {
       if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
       continue;
     }
-    const int t = (int)tl;  // tiles of one image fit in 32 bits
-#define CT_BATCH_CASE(KK)                                   \
-  case KK:                                                  \
-    if (im.ty == 1) batch_tile<KK, 1>(im, t, smem);         \
-    else if (im.ty == 2) batch_tile<KK, 2>(im, t, smem);    \
-    else batch_tile<KK, 4>(im, t, smem);                    \
-    break;
-    switch (im.k) {
-      CT_BATCH_CASE(1)
-      CT_BATCH_CASE(3)
-      CT_BATCH_CASE(5)
-      CT_BATCH_CASE(7)
-      CT_BATCH_CASE(9)
-      CT_BATCH_CASE(11)
-      CT_BATCH_CASE(13)
-      CT_BATCH_CASE(15)
-      CT_BATCH_CASE(17)
-      default:
-        if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
-        break;
-    }
-#undef CT_BATCH_CASE
+    run_tile<CLS>(im, (int)tl, smem, a.status);  // tiles of one image fit in 32 bits
+  }
+}
+
+const void* batched_kernel_fn(int cls) {
+  switch (cls) {
+    case 0: return (const void*)batched_conv_kernel<0>;
+    case 1: return (const void*)batched_conv_kernel<1>;
+    default: return (const void*)batched_conv_kernel<2>;
   }
 }
 
@@ -96,6 +122,88 @@ int size_class(int h, int w) { return (long long)h * w >= 512LL * 512LL ? 1 : 0;
 
 }  // namespace
 
+int plan_batch(const BatchImage* table, int n, BatchPlan* plan) {
+  *plan = BatchPlan();
+  int dev = 0, sms = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= 64) return CT_ENOTSUP;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+          cudaSuccess)
+    return cuda_status(e);
+  {
+    // once per device: every class kernel may use the device's whole opt-in
+    // shared memory (a per-plan value could undercut another live plan)
+    static std::mutex mu;
+    static bool raised[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!raised[dev]) {
+      for (int c = 0; c < kBatchClasses; ++c) {
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, batched_kernel_fn(c))) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(batched_kernel_fn(c),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      optin - (int)fa.sharedSizeBytes)) != cudaSuccess)
+          return cuda_status(e);
+      }
+      raised[dev] = true;
+    }
+  }
+  for (int q = 1; q < n; ++q)
+    if (batch_class_of(table[q].k) < batch_class_of(table[q - 1].k)) return CT_EINVAL;
+  int q = 0;
+  for (int c = 0; c < kBatchClasses; ++c) {
+    BatchClassLaunch& L = plan->cls[c];
+    L.lo = q;
+    while (q < n && batch_class_of(table[q].k) == c) {
+      const BatchImage& im = table[q];
+      L.items += (long long)im.tiles_x * im.tiles_y;
+      L.smem = std::max(L.smem, batch_smem_bytes(im.k, im.bx, im.ty));
+      ++q;
+    }
+    L.n = q - L.lo;
+    if (L.n == 0) continue;
+    L.item_base = table[L.lo].first_item;
+    L.smem = std::max<size_t>(L.smem, 16);
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, batched_kernel_fn(c))) != cudaSuccess)
+      return cuda_status(e);
+    if (L.smem + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_fn(c),
+                                                           kBatchThreads, L.smem)) != cudaSuccess)
+      return cuda_status(e);
+    if (per_sm < 1) return CT_ECONFIG;
+    L.grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sms, L.items));
+    plan->total_grid += L.grid;
+    plan->max_smem = std::max(plan->max_smem, L.smem);
+  }
+  return CT_OK;
+}
+
+int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigned* counters,
+                       unsigned* status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * kBatchClasses, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int c = 0; c < kBatchClasses; ++c) {
+    const BatchClassLaunch& L = plan.cls[c];
+    if (L.n == 0) continue;
+    BatchArgs a;
+    a.images = d_table + L.lo;
+    a.n_images = L.n;
+    a.n_items = L.items;
+    a.item_base = L.item_base;
+    a.counter = counters + c;
+    a.status = status;
+    if (c == 0) batched_conv_kernel<0><<<L.grid, kBatchThreads, L.smem, s>>>(a);
+    else if (c == 1) batched_conv_kernel<1><<<L.grid, kBatchThreads, L.smem, s>>>(a);
+    else batched_conv_kernel<2><<<L.grid, kBatchThreads, L.smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+  }
+  return CT_OK;
+}
+
 }  // namespace convtune
 
 using namespace convtune;
@@ -110,8 +218,9 @@ struct ct_batch {
   float* d_filters = nullptr;
   unsigned* d_counter = nullptr;
   long long n_items = 0;
-  size_t smem = 0;
-  int grid = 0;
+  BatchPlan plan;        // class ranges, shared memory and grids
+  size_t smem = 0;       // largest class's dynamic shared memory
+  int grid = 0;          // CTAs over all class launches
   double flop = 0;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -126,22 +235,13 @@ struct ct_batch {
 
 namespace {
 
-// Enqueue one batched launch: counter reset + persistent kernel.
+// Enqueue one batched run: counter reset + one persistent kernel per class.
 int enqueue_batch(ct_batch* b, cudaStream_t s) {
   if (b->n_items == 0) return CT_OK;
   int err = CT_OK;
   unsigned* status = device_status_word(&err);
   if (!status) return err;
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
-  if (e != cudaSuccess) return cuda_status(e);
-  BatchArgs a;
-  a.images = b->d_images;
-  a.n_images = (int)b->host_images.size();
-  a.n_items = b->n_items;
-  a.counter = b->d_counter;
-  a.status = status;
-  batched_conv_kernel<<<b->grid, kBatchThreads, b->smem, s>>>(a);
-  return cuda_status(cudaGetLastError());
+  return enqueue_batch_plan(b->plan, b->d_images, b->d_counter, status, s);
 }
 
 // The plain comparison: one ct_conv2d_run per image, configuration from the
@@ -225,19 +325,16 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
     return std::make_pair(imgs[x].k, cx) < std::make_pair(imgs[y].k, cy);
   });
   long long first = 0;
-  size_t smem = 0;
   size_t filt_floats = 0;
   for (int j : idx) {
     BatchImage im = imgs[j];
     im.first_item = first;
     first += (long long)im.tiles_x * im.tiles_y;
-    smem = std::max(smem, batch_smem_bytes(im.k, im.bx, im.ty));
     filt_floats += (size_t)im.k * round_up(im.k, 4);
     b->host_images.push_back(im);
     b->order.push_back(order[j]);
   }
   b->n_items = first;
-  b->smem = std::max<size_t>(smem, 16);
   // device copies: padded taps, then the table pointing at them
   cudaError_t e;
   std::vector<float> padded(std::max<size_t>(filt_floats, 1), 0.0f);
@@ -266,30 +363,11 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
     return cuda_status(e);
   if ((e = cudaMalloc(&b->d_counter, 256)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(b->d_counter, 0, 256)) != cudaSuccess) return cuda_status(e);
-  // persistent grid: resident CTAs per SM x SMs, capped by the work
-  if (b->smem > 48 * 1024) {
-    // the cap is per kernel and shared by every plan: raise it to the device
-    // limit (a per-plan value could undercut another live plan's graph)
-    int optin = 0;
-    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
-                                    b->device)) != cudaSuccess)
-      return cuda_status(e);
-    cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, batched_conv_kernel)) != cudaSuccess)
-      return cuda_status(e);
-    if (b->smem + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
-    e = cudaFuncSetAttribute(batched_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
-    if (e != cudaSuccess) return cuda_status(e);
-  }
-  int per_sm = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
-                                                         kBatchThreads, b->smem)) != cudaSuccess)
-    return cuda_status(e);
-  if (per_sm < 1) return CT_ECONFIG;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device)) != cudaSuccess)
-    return cuda_status(e);
-  b->grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sms, b->n_items));
+  // persistent grids: resident CTAs per SM x SMs per class, capped by the work
+  const int rc = plan_batch(b->host_images.data(), (int)b->host_images.size(), &b->plan);
+  if (rc != CT_OK) return rc;
+  b->grid = b->plan.total_grid;
+  b->smem = std::max<size_t>(b->plan.max_smem, 16);
   return CT_OK;
 }
 
@@ -476,7 +554,6 @@ constexpr size_t kNoAllocBytes = kNoAllocHeaderBytes + kNoAllocTableBytes + kNoA
 struct NoAllocDevice {
   bool ready = false;
   unsigned char* base = nullptr;  // device address of the scratch array
-  int sms = 0;
 };
 
 std::mutex g_noalloc_mu;
@@ -504,25 +581,12 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   NoAllocDevice nd;
   {
     // once per device, with that device current: resolve the array's device
-    // address and lift the kernel's shared-memory cap
+    // address (the class kernels' shared-memory caps are raised by the plan)
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     NoAllocDevice& d = g_noalloc_dev[dev];
     if (!d.ready) {
       void* p = nullptr;
       if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return cuda_status(e);
-      int optin = 0;
-      if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
-          cudaSuccess)
-        return cuda_status(e);
-      cudaFuncAttributes fa;
-      if ((e = cudaFuncGetAttributes(&fa, batched_conv_kernel)) != cudaSuccess)
-        return cuda_status(e);
-      if ((e = cudaFuncSetAttribute(batched_conv_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin - (int)fa.sharedSizeBytes)) != cudaSuccess)
-        return cuda_status(e);
-      if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-        return cuda_status(e);
       d.base = static_cast<unsigned char*>(p);
       d.ready = true;
     }
@@ -554,12 +618,12 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   if (m == 0) return CT_OK;
 
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned* counter = reinterpret_cast<unsigned*>(nd.base);
-  unsigned* status = counter + 1;
+  // header: one work counter per filter-side class, then the status word
+  unsigned* counters = reinterpret_cast<unsigned*>(nd.base);
+  unsigned* status = counters + kBatchClasses;
   BatchImage* d_table = reinterpret_cast<BatchImage*>(nd.base + kNoAllocHeaderBytes);
   float* d_taps = reinterpret_cast<float*>(nd.base + kNoAllocHeaderBytes + kNoAllocTableBytes);
   long long first = 0;
-  size_t smem = 16;
   for (int q = 0; q < m; ++q) {
     const ct_batch_item& it = items[idx[q]];
     BatchImage& im = t_noalloc_table[q];
@@ -588,7 +652,6 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
     im.tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
     im.first_item = first;
     first += (long long)im.tiles_x * im.tiles_y;
-    smem = std::max(smem, batch_smem_bytes(it.k, bx, ty));
     // taps: k rows padded to round_up(k, 4) floats (the padding is never used
     // as a tap), copied straight from the caller's host array
     const int kp = round_up(it.k, 4);
@@ -601,23 +664,13 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   if ((e = cudaMemcpyAsync(d_table, t_noalloc_table, sizeof(BatchImage) * m,
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_status(e);
-  // the work counter must start at zero; the status word is cleared too
-  if ((e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), s)) != cudaSuccess)
+  // the status word starts clear (the counters are zeroed with the launches)
+  if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), s)) != cudaSuccess)
     return cuda_status(e);
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
-                                                         kBatchThreads, smem)) != cudaSuccess)
-    return cuda_status(e);
-  if (per_sm < 1) return CT_ECONFIG;
-  BatchArgs a;
-  a.images = d_table;
-  a.n_images = m;
-  a.n_items = first;
-  a.counter = counter;
-  a.status = status;
-  const int grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * nd.sms, first));
-  batched_conv_kernel<<<grid, kBatchThreads, smem, s>>>(a);
-  return cuda_status(cudaGetLastError());
+  BatchPlan plan;
+  const int rc = plan_batch(t_noalloc_table, m, &plan);
+  if (rc != CT_OK) return rc;
+  return enqueue_batch_plan(plan, d_table, counters, status, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -656,33 +709,6 @@ int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, 
   im->tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
   *smem = std::max(*smem, batch_smem_bytes(it.k, bx, ty));
   return CT_OK;
-}
-
-int launch_batched_kernel(const BatchArgs& a, size_t smem, int sms, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t raised = cudaSuccess;
-  std::call_once(once, [] {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa;
-    raised = cudaGetDevice(&dev);
-    if (raised == cudaSuccess)
-      raised = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (raised == cudaSuccess) raised = cudaFuncGetAttributes(&fa, batched_conv_kernel);
-    if (raised == cudaSuccess)
-      raised = cudaFuncSetAttribute(batched_conv_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin - (int)fa.sharedSizeBytes);
-  });
-  if (raised != cudaSuccess) return cuda_status(raised);
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_conv_kernel,
-                                                                kBatchThreads, smem);
-  if (e != cudaSuccess) return cuda_status(e);
-  if (per_sm < 1) return CT_ECONFIG;
-  const int grid =
-      (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sms, a.n_items));
-  batched_conv_kernel<<<grid, kBatchThreads, smem, s>>>(a);
-  return cuda_status(cudaGetLastError());
 }
 
 }  // namespace convtune

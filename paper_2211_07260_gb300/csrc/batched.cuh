@@ -27,12 +27,21 @@ struct alignas(16) BatchImage {
 };
 
 struct BatchArgs {
-  const BatchImage* images;
+  const BatchImage* images;  // this launch's images (a contiguous run of the table)
   int n_images;
-  long long n_items;
-  unsigned* counter;     // work counter, zero at launch
-  unsigned* status;      // device status word
+  long long n_items;         // work items of these images
+  long long item_base;       // first_item of images[0]: item w is table item item_base + w
+  unsigned* counter;         // work counter, zero at launch
+  unsigned* status;          // device status word
 };
+
+// Filter sides are split into classes, one persistent kernel each: a kernel's
+// register allocation is that of its largest body, and the small-filter
+// bodies (latency-bound) need far fewer registers than the 13..17 ones, so
+// separate kernels keep more of their CTAs resident (GB300: 64, 80 and 124
+// registers -> 4, 3 and 2 CTAs of 256 threads per SM).
+constexpr int kBatchClasses = 3;
+__host__ __device__ constexpr int batch_class_of(int k) { return k <= 7 ? 0 : (k <= 11 ? 1 : 2); }
 
 // Fields stage_tile_cp_async() reads.
 struct BatchStage {

@@ -14,8 +14,29 @@ namespace convtune {
 int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, BatchImage* im,
                           size_t* smem);
 
-// Launch the persistent batched kernel over a device table (counter must be
-// zero), occupancy-sized grid.
-int launch_batched_kernel(const BatchArgs& a, size_t smem, int sms, cudaStream_t s);
+// Launch plan of a host copy of a batch table: the table must be ordered by
+// filter-side class (batch_class_of, ascending); each class's contiguous run
+// of images gets its own persistent kernel, with that run's shared memory and
+// an occupancy-sized grid.  The first call per device raises the class
+// kernels' shared-memory caps (make it before any stream capture).
+struct BatchClassLaunch {
+  int lo = 0, n = 0;          // run of the table
+  long long items = 0;        // work items of the run
+  long long item_base = 0;    // first_item of its first image
+  size_t smem = 0;            // dynamic shared memory per CTA
+  int grid = 0;               // persistent CTAs
+};
+struct BatchPlan {
+  BatchClassLaunch cls[kBatchClasses];
+  int total_grid = 0;
+  size_t max_smem = 0;
+};
+int plan_batch(const BatchImage* table, int n, BatchPlan* plan);
+
+// Enqueue a planned batch over the device copy of the same table: zeroes the
+// kBatchClasses work counters at `counters`, then launches the class kernels
+// one after another on `s`.
+int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigned* counters,
+                       unsigned* status, cudaStream_t s);
 
 }  // namespace convtune

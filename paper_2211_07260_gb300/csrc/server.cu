@@ -199,6 +199,11 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
       if ((rc = ct_conv2d_run(&p, &c, sl.s)) != CT_OK) return rc;
     }
   } else {
+    // the table runs in filter-side class order (one persistent kernel per
+    // class); the caller's order of `batch` does not matter beyond this
+    std::stable_sort(batch.begin(), batch.end(), [](const Request* x, const Request* y) {
+      return batch_class_of(x->k) < batch_class_of(y->k);
+    });
     size_t smem = 16;
     long long first = 0;
     for (size_t q = 0; q < batch.size(); ++q) {
@@ -230,18 +235,13 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
     if ((e = cudaMemcpyAsync(sl.d_table, sl.h_table, sizeof(BatchImage) * n,
                              cudaMemcpyHostToDevice, sl.s)) != cudaSuccess)
       return cuda_status(e);
-    if ((e = cudaMemsetAsync(sl.d_counter, 0, sizeof(unsigned), sl.s)) != cudaSuccess)
-      return cuda_status(e);
     int err = CT_OK;
     unsigned* status = device_status_word(&err);
     if (!status) return err;
-    BatchArgs a;
-    a.images = sl.d_table;
-    a.n_images = (int)n;
-    a.n_items = first;
-    a.counter = sl.d_counter;
-    a.status = status;
-    if ((rc = launch_batched_kernel(a, smem, sms, sl.s)) != CT_OK) return rc;
+    BatchPlan plan;
+    if ((rc = plan_batch(sl.h_table, (int)n, &plan)) != CT_OK) return rc;
+    if ((rc = enqueue_batch_plan(plan, sl.d_table, sl.d_counter, status, sl.s)) != CT_OK)
+      return rc;
   }
   // outputs back: only the out_w computed columns of each row (the caller's
   // padding columns are left untouched)

@@ -42,7 +42,8 @@ def test_batched_equals_plain_bitwise_and_oracle(tiles):
     ents_p, outs_p = device_entries(probs)
     with api.Batch(ents, t) as b, api.Batch(ents_p, t) as bp:
         st = b.info()
-        assert st["n_images"] == len(probs) and st["n_items"] > st["grid"] > 0
+        # one persistent kernel per filter-side class, each grid capped by its items
+        assert st["n_images"] == len(probs) and st["n_items"] >= st["grid"] > 0
         b.run()
         bp.run_plain()
         torch.cuda.synchronize()
