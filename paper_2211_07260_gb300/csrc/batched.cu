@@ -54,26 +54,44 @@ __device__ __forceinline__ void run_tile(const BatchImage& im, int t, float* sme
   if (threadIdx.x == 0) atomicOr(status, kStatusBadItem);
 }
 
+// resident CTAs per SM each class kernel is compiled for (registers <= 64,
+// 85, 128 per thread)
+__host__ __device__ constexpr int batch_class_min_ctas(int cls) { return cls == 0 ? 4 : (cls == 1 ? 3 : 2); }
+
 template <int CLS>
-__global__ void __launch_bounds__(kBatchThreads) batched_conv_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
+    batched_conv_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* smem = reinterpret_cast<float*>(smem_raw);
   __shared__ long long s_item;
   __shared__ int s_img;
+  // thread 0 claims each work item one tile ahead (the atomic's round trip
+  // overlaps the current tile) and remembers the last item's image (most
+  // items a CTA claims in a row lie in the same large image)
+  long long next = 0;
+  int last_img = 0;
+  if (threadIdx.x == 0) next = (long long)atomicAdd(a.counter, 1u);
   for (;;) {
     if (threadIdx.x == 0) {
-      const long long w = (long long)atomicAdd(a.counter, 1u);
+      const long long w = next;
       int img = -1;
       if (w < a.n_items) {
-        // last image whose first item is <= the table item
+        next = (long long)atomicAdd(a.counter, 1u);
         const long long gw = a.item_base + w;
-        int lo = 0, hi = a.n_images - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) / 2;
-          if (a.images[mid].first_item <= gw) lo = mid;
-          else hi = mid - 1;
+        const BatchImage& c = a.images[last_img];
+        if (gw >= c.first_item && gw < c.first_item + (long long)c.tiles_x * c.tiles_y) {
+          img = last_img;
+        } else {
+          // last image whose first item is <= the table item
+          int lo = 0, hi = a.n_images - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (a.images[mid].first_item <= gw) lo = mid;
+            else hi = mid - 1;
+          }
+          img = lo;
         }
-        img = lo;
+        last_img = img;
       }
       s_item = w;
       s_img = img;
