@@ -268,14 +268,15 @@ def run_batched(args, world, rank, local):
         "ms_per_step": t_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "images": st["n_images"], "tiles": st["n_items"],
-                   "persistent_ctas": st["grid"], "tiles_source": src,
+                   "persistent_ctas": st["grid"], "class_launches": st["launches"],
+                   "tiles_source": src,
                    "l2": "inputs 1.5 GB > L2", "parallelism": f"replicas x{world}"},
         "gflop_per_j": rb["gflops_per_j"],
         "batched": {"gflops": rb["gflops"], "gflop_per_j": rb["gflops_per_j"],
                     "power_w_mean": rb["power_w_mean"], "flags": rb["flags"]},
         "plain_per_image": {"gflops": rp["gflops"], "gflop_per_j": rp["gflops_per_j"],
                             "power_w_mean": rp["power_w_mean"], "flags": rp["flags"]},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * st["launches"],
     }
     print(json.dumps(out))
 

@@ -480,10 +480,12 @@ typedef struct {
 typedef struct {
   int n_images;       /* non-empty images                                   */
   long long n_items;  /* output tiles                                       */
-  int grid;           /* persistent CTAs                                    */
-  long smem_bytes;    /* dynamic shared memory per CTA                      */
+  int grid;           /* persistent CTAs, over all kernel launches          */
+  long smem_bytes;    /* dynamic shared memory per CTA (largest launch)     */
   double flop;        /* useful FLOP per batch                              */
   double bytes;       /* algorithmic bytes per batch (inputs, outputs, taps) */
+  int launches;       /* kernel launches per run: one persistent kernel per
+                         filter-side class present (sides 1-7, 9-11, 13-17) */
 } ct_batch_stats;
 
 typedef struct ct_batch ct_batch;  /* opaque plan */

@@ -606,7 +606,8 @@ class CtBatchTiles(ctypes.Structure):
 
 class CtBatchStats(ctypes.Structure):
     _fields_ = [("n_images", c_int), ("n_items", ctypes.c_longlong), ("grid", c_int),
-                ("smem_bytes", c_long), ("flop", c_double), ("bytes", c_double)]
+                ("smem_bytes", c_long), ("flop", c_double), ("bytes", c_double),
+                ("launches", c_int)]
 
 
 def batch_items(entries):

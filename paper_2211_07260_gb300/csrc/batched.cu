@@ -451,6 +451,7 @@ int ct_batch_info(const ct_batch* b, ct_batch_stats* st) {
   st->grid = b->grid;
   st->smem_bytes = (long)b->smem;
   st->flop = b->flop;
+  for (int c = 0; c < kBatchClasses; ++c) st->launches += b->plan.cls[c].n > 0 ? 1 : 0;
   for (const BatchImage& im : b->host_images)
     st->bytes += 4.0 * ((double)im.in_h * im.in_w + (double)im.out_h * im.out_w + im.k * im.k);
   return CT_OK;

@@ -44,6 +44,8 @@ def test_batched_equals_plain_bitwise_and_oracle(tiles):
         st = b.info()
         # one persistent kernel per filter-side class, each grid capped by its items
         assert st["n_images"] == len(probs) and st["n_items"] >= st["grid"] > 0
+        classes = {0 if p.filt.shape[0] <= 7 else 1 if p.filt.shape[0] <= 11 else 2 for p in probs}
+        assert st["launches"] == len(classes)
         b.run()
         bp.run_plain()
         torch.cuda.synchronize()
