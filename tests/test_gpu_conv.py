@@ -209,6 +209,32 @@ def test_host_entry_point_explicit_bands():
     assert np.all(out == -1.0)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_point_repeated_calls(pinned):
+    # repeated calls on the same buffers (the library's device buffers and
+    # streams are reused): every call must read the caller's current input
+    # and give the same bits as a device run
+    h, w, k = 1200, 256, 9
+    cfg = api.Config(32, 4, 4, 2, api.STAGE_TMA, api.FILTER_CONST, 4)
+    base = synth.conv_problem(h, w, k, seed=21)
+    inp = np.empty_like(base.inp)
+    out = np.empty((h, w), np.float32)
+    if pinned:
+        inp = torch.from_numpy(inp).pin_memory().numpy()
+        out = torch.from_numpy(out).pin_memory().numpy()
+    for rep in range(4):
+        prob = synth.conv_problem(h, w, k, seed=[21, rep])
+        prob = synth.ConvProblem(inp=prob.inp, in_w=prob.in_w, filt=base.filt,
+                                 out_h=prob.out_h, out_w=prob.out_w)
+        inp[...] = prob.inp
+        out.fill(-1.0)
+        api.conv2d_run_host(inp, base.filt, out, h, w, cfg)
+        d_in, full, d_out = to_device(prob)
+        run(prob, cfg, d_in, d_out)
+        assert np.array_equal(out, full.cpu().numpy()[:, :w]), rep
+    assert max_rel_err(out, oracle_ref(prob)) <= MAX_REL
+
+
 @pytest.mark.parametrize("which", ["1024x1024_k7", "4096x4096_k17"])
 def test_full_size_workloads(which):
     if which == "1024x1024_k7":
