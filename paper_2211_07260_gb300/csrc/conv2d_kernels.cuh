@@ -36,7 +36,7 @@ namespace convtune {
 // Launch arguments.  The filter travels by value in the parameter space, i.e.
 // in the constant bank.
 template <int NTAPS>
-struct alignas(64) ConvArgs {
+struct alignas(128) ConvArgs {  // (the tensor map needs 128-byte alignment)
   CUtensorMap tmap;          // TMA descriptor of the padded input (TMA staging)
   const float* in;           // padded input, in_h rows of in_pitch floats
   float* out;                // output, out_h rows of out_pitch floats
@@ -157,15 +157,6 @@ template <class Args>
 __device__ __forceinline__ void stage_tile_cp_async(const Args& a, float* tile, int gx0, int gy0) {
   issue_tile_cp_async(a, tile, gx0, gy0);
   cp_async_wait_all();
-}
-
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-// Wait until at most one committed group is still in flight.
-__device__ __forceinline__ void cp_async_wait_one() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* mbar) {

@@ -587,7 +587,7 @@ int ct_device_info_get(ct_device_info* out) {
   out->cc_minor = prop.minor;
   out->max_smem_optin_bytes = (int)prop.sharedMemPerBlockOptin;
   out->l2_bytes = prop.l2CacheSize;
-  snprintf(out->name, sizeof(out->name), "%s", prop.name);
+  snprintf(out->name, sizeof(out->name), "%.*s", (int)sizeof(out->name) - 1, prop.name);
   int khz = 0;
   if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) == cudaSuccess)
     out->sm_clock_max_mhz = khz / 1000.0;

@@ -126,7 +126,6 @@ using namespace convtune;
 struct ct_server {
   ct_server_options opt;
   int device = 0;
-  int sms = 0;
   unsigned char* pool = nullptr;
   size_t pool_bytes = 0;
   unsigned char* slot_mem = nullptr;
@@ -370,7 +369,6 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
   if (!sv) return CT_ENOMEM;
   sv->opt = *opt;
   cudaError_t e = cudaGetDevice(&sv->device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, sv->device);
   // the request pool never exceeds 90 % of the device memory free right now
   size_t free_b = 0, total_b = 0;
   if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
