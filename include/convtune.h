@@ -450,17 +450,20 @@ int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
 
 /*
  * Many correlations of uneven sizes and odd filter sides (1..17) in one
- * persistent launch.  A plan copies the taps and an image table to the
- * device (library scratch, freed by ct_batch_destroy), sorts the images by
- * (filter side, size class) and captures [work-counter reset + persistent
- * kernel] into a CUDA graph; ct_batch_run replays it (one host call and one
- * graph launch per batch).  CTAs of 256 threads, resident-occupancy x SM
- * count of them, take output tiles from a global atomic counter; each tile
+ * persistent launch per filter-side class (sides 1-7, 9-11, 13-17: separate
+ * kernels so that each keeps its own register budget).  A plan copies the
+ * taps and an image table to the device (library scratch, freed by
+ * ct_batch_destroy), sorts the images by (filter side, size class) and
+ * captures [work-counter reset + the persistent class kernels] into a CUDA
+ * graph; ct_batch_run replays it (one host call and one graph launch per
+ * batch).  CTAs of 256 threads, resident-occupancy x SM count of them per
+ * class kernel, take output tiles from a global atomic counter; each tile
  * uses the tap order of the plain kernel, so outputs are bitwise identical
  * to ct_conv2d_run.  Tiles are 4 outputs wide per thread; per bucket
  * (size class: output area < or >= 512^2; filter side) the block width and
- * tile height come from ct_batch_tiles (0 entries: 32 x 8 threads, tile_y
- * 2).
+ * tile height come from ct_batch_tiles (0 or invalid entries: 32 x 8
+ * threads, tile_y 2).  The plain comparison runs each image with the same
+ * block and min(tile_y, 4).
  */
 typedef struct {
   const float* in;    /* device, padded input: out_h+k-1 rows of in_pitch   */
@@ -474,7 +477,7 @@ typedef struct {
 
 typedef struct {
   int block_x[2][18]; /* [size class][k]: 16, 32, 64 or 128 (block_y = 256/block_x) */
-  int tile_y[2][18];  /* [size class][k]: 1, 2 or 4                         */
+  int tile_y[2][18];  /* [size class][k]: 1, 2 or 4; also 8 for k <= 3     */
 } ct_batch_tiles;
 
 typedef struct {
@@ -506,9 +509,10 @@ int ct_measure_batch(ct_batch* b, int plain, const ct_measure_options* opt, void
                      ct_record* out);
 /*
  * Per-bucket tile tuning: for every (size class, filter side) present, the
- * median-area image is measured alone as a one-image batch for block_x in
- * {16, 32, 64, 128} x tile_y in {1, 2, 4} and the objective's best is kept.
- * records (optional, 12 per bucket) receive the measurements.
+ * bucket's images are measured together as one batch for block_x in
+ * {16, 32, 64, 128} x tile_y in {1, 2, 4} (and 8 for k <= 3) and the
+ * objective's best is kept.  records (optional: 16 per bucket with k <= 3,
+ * 12 per other bucket) receive the measurements.
  */
 int ct_batch_tune(const ct_batch_item* items, int n, int objective,
                   const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,

@@ -22,7 +22,12 @@ template <int KK>
 __device__ __forceinline__ void run_tile_k(const BatchImage& im, int t, float* smem) {
   if (im.ty == 1) batch_tile<KK, 1>(im, t, smem);
   else if (im.ty == 2) batch_tile<KK, 2>(im, t, smem);
-  else batch_tile<KK, 4>(im, t, smem);
+  else if constexpr (KK <= kBatchMaxK8) {
+    if (im.ty == 8) batch_tile<KK, 8>(im, t, smem);
+    else batch_tile<KK, 4>(im, t, smem);
+  } else {
+    batch_tile<KK, 4>(im, t, smem);
+  }
 }
 
 // One tile of a class-CLS image; a filter side outside the class (a table
@@ -132,8 +137,9 @@ size_t batch_smem_bytes(int k, int bx, int ty) {
   return sizeof(float) * (size_t)(filt + tile_w * tile_h);
 }
 
-bool valid_tile(int bx, int ty) {
-  return (bx == 16 || bx == 32 || bx == 64 || bx == 128) && (ty == 1 || ty == 2 || ty == 4);
+bool valid_tile(int bx, int ty, int k) {
+  return (bx == 16 || bx == 32 || bx == 64 || bx == 128) &&
+         (ty == 1 || ty == 2 || ty == 4 || (ty == 8 && k <= kBatchMaxK8));
 }
 
 int size_class(int h, int w) { return (long long)h * w >= 512LL * 512LL ? 1 : 0; }
@@ -281,7 +287,7 @@ int enqueue_plain(ct_batch* b, cudaStream_t s) {
     c.block_x = im.bx;
     c.block_y = kBatchThreads / im.bx;
     c.tile_x = kBatchTileX;
-    c.tile_y = im.ty;
+    c.tile_y = std::min(im.ty, 4);  // (the single-image kernel's tiles are at most 4 high)
     c.staging = CT_STAGE_SMEM;
     c.filter_mem = CT_FILTER_CONST;
     c.vec_width = im.vw;
@@ -319,7 +325,7 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
     im.k = it.k;
     const int cls = size_class(it.out_h, it.out_w);
     int bx = 32, ty = 2;
-    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k])) {
+    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k], it.k)) {
       bx = tiles->block_x[cls][it.k];
       ty = tiles->tile_y[cls][it.k];
     }
@@ -494,29 +500,33 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
     if (items[i].k < 1 || items[i].k > kMaxK || !(items[i].k & 1)) return CT_EINVAL;
     bucket[size_class(items[i].out_h, items[i].out_w) * (kMaxK + 1) + items[i].k].push_back(i);
   }
-  const int bxs[4] = {16, 32, 64, 128}, tys[3] = {1, 2, 4};
+  const int bxs[4] = {16, 32, 64, 128}, tys[4] = {1, 2, 4, 8};
+  auto n_ty = [](int k) { return k <= kBatchMaxK8 ? 4 : 3; };
   int written = 0, needed = 0;
-  for (auto& v : bucket) needed += v.empty() ? 0 : 12;
+  for (size_t q = 0; q < bucket.size(); ++q)
+    needed += bucket[q].empty() ? 0 : 4 * n_ty((int)(q % (kMaxK + 1)));
   *n_records = needed;
   if (records && cap < needed) return CT_ENOMEM;
   for (int cls = 0; cls < 2; ++cls) {
     for (int k = 1; k <= kMaxK; k += 2) {
       std::vector<int>& v = bucket[cls * (kMaxK + 1) + k];
       if (v.empty()) continue;
-      std::sort(v.begin(), v.end(), [&](int x, int y) {
-        return (long long)items[x].out_h * items[x].out_w <
-               (long long)items[y].out_h * items[y].out_w;
-      });
-      const ct_batch_item& rep = items[v[v.size() / 2]];
+      // every image of the bucket, as one batch: a launch the size of the
+      // bucket's share of the real batch (one median image alone measured
+      // launch and tail effects more than the tile, and its pick varied from
+      // run to run)
+      std::vector<ct_batch_item> sub;
+      for (int i : v) sub.push_back(items[i]);
       std::vector<ct_record> recs;
       for (int bx : bxs)
-        for (int ty : tys) {
+        for (int qt = 0; qt < n_ty(k); ++qt) {
+          const int ty = tys[qt];
           ct_batch_tiles t;
           memset(&t, 0, sizeof(t));
           t.block_x[cls][k] = bx;
           t.tile_y[cls][k] = ty;
           ct_batch* b = nullptr;
-          int rc = ct_batch_create(&rep, 1, &t, &b);
+          int rc = ct_batch_create(sub.data(), (int)sub.size(), &t, &b);
           if (rc != CT_OK) return rc;
           MeasureUnit u;
           u.kind = CT_UNIT_CONV;
@@ -658,7 +668,7 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
     im.k = it.k;
     const int cls = size_class(it.out_h, it.out_w);
     int bx = 32, ty = 2;
-    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k])) {
+    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k], it.k)) {
       bx = tiles->block_x[cls][it.k];
       ty = tiles->tile_y[cls][it.k];
     }
@@ -715,7 +725,7 @@ int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, 
   im->k = it.k;
   const int cls = size_class(it.out_h, it.out_w);
   int bx = 32, ty = 2;
-  if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k])) {
+  if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k], it.k)) {
     bx = tiles->block_x[cls][it.k];
     ty = tiles->tile_y[cls][it.k];
   }

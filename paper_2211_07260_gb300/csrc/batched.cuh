@@ -13,6 +13,10 @@ namespace convtune {
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchTileX = 4;
+// Filter sides up to this one may also take 8-row tiles (their bodies are
+// small and latency-bound; 8-row tiles for 5 x 5 and 7 x 7 measured no
+// faster, and their registers would cost the class kernel a resident CTA).
+constexpr int kBatchMaxK8 = 3;
 
 // One image of the batch (device table entry).
 struct alignas(16) BatchImage {

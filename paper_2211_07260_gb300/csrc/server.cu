@@ -191,7 +191,7 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
       c.block_x = im.bx;
       c.block_y = kBatchThreads / im.bx;
       c.tile_x = kBatchTileX;
-      c.tile_y = im.ty;
+      c.tile_y = std::min(im.ty, 4);  // (the single-image kernel's tiles are at most 4 high)
       c.staging = CT_STAGE_SMEM;
       c.filter_mem = CT_FILTER_CONST;
       c.vec_width = im.vw;

@@ -29,7 +29,7 @@ def mixed_problems(n=40, seed=5):
     return probs
 
 
-@pytest.mark.parametrize("tiles", [None, "varied"])
+@pytest.mark.parametrize("tiles", [None, "varied", "tall"])
 def test_batched_equals_plain_bitwise_and_oracle(tiles):
     probs = mixed_problems()
     t = None
@@ -38,6 +38,10 @@ def test_batched_equals_plain_bitwise_and_oracle(tiles):
         for i, k in enumerate(range(1, 18, 2)):
             t[(0, k)] = ((16, 32, 64, 128)[i % 4], (1, 2, 4)[i % 3])
             t[(1, k)] = ((128, 64, 32, 16)[i % 4], (4, 1, 2)[i % 3])
+    elif tiles == "tall":
+        # 8-row tiles (filter sides <= 3 only; larger sides fall back to the
+        # default tile)
+        t = {(c, k): (32 if k < 5 else 64, 8) for c in (0, 1) for k in range(1, 18, 2)}
     ents, outs = device_entries(probs)
     ents_p, outs_p = device_entries(probs)
     with api.Batch(ents, t) as b, api.Batch(ents_p, t) as bp:
@@ -99,9 +103,10 @@ def test_bucket_tuning_and_measurement():
     tiles, recs = api.batch_tune(ents, "energy", api.measure_options(window_s=0.2, warmup_s=0.05))
     ks = {(int(p.out_h * p.out_w >= 512 * 512), p.fh) for p in probs}
     assert set(tiles) == ks
-    assert len(recs) == 12 * len(ks)
+    # 4 block widths x tile heights 1, 2, 4 (and 8 for filter sides <= 3)
+    assert len(recs) == sum(16 if k <= 3 else 12 for _, k in ks)
     for (cls, k), (bx, ty) in tiles.items():
-        assert bx in (16, 32, 64, 128) and ty in (1, 2, 4)
+        assert bx in (16, 32, 64, 128) and ty in ((1, 2, 4, 8) if k <= 3 else (1, 2, 4))
     with api.Batch(ents, tiles) as b:
         rb = b.measure(False, api.measure_options(window_s=0.2, warmup_s=0.05))
         rp = b.measure(True, api.measure_options(window_s=0.2, warmup_s=0.05))
