@@ -300,6 +300,19 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
   return CT_OK;
 }
 
+int prime_conv_kernel(int k, const ct_config& c) {
+  if (k < 1 || k > kMaxK || !(k & 1)) return CT_EINVAL;
+  const void* fn = pick_specialised(k, c.tile_x, c.tile_y, c.staging != CT_STAGE_DIRECT,
+                                    c.filter_mem == CT_FILTER_SHARED,
+                                    c.block_x * c.block_y >= kRingRemFirstThreads);
+  if (!fn) return CT_ECONFIG;
+  int err = CT_OK;
+  DeviceState* st = current_state(nullptr, &err);
+  if (!st) return err;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return cuda_status(raise_smem_cap(st, fn));  // queries (and so loads) the kernel
+}
+
 int launch_plan(ConvPlan& plan, cudaStream_t s) {
   if (plan.empty) return CT_OK;
   int err = CT_OK;

@@ -33,6 +33,11 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
 // Launch a resolved plan on a stream.
 int launch_plan(ConvPlan& plan, cudaStream_t s);
 
+// Load the specialised K x K kernel variant of configuration c and raise its
+// shared-memory cap now, ahead of its first launch: kernel code is loaded on
+// first use, which otherwise stalls that launch's caller for milliseconds.
+int prime_conv_kernel(int k, const ct_config& c);
+
 // Device status word of the current device (allocated on first use).
 unsigned* device_status_word(int* err);
 
