@@ -19,27 +19,28 @@
 namespace convtune {
 
 template <int KK>
-__device__ __forceinline__ void run_tile_k(const BatchImage& im, int t, float* smem) {
-  if (im.ty == 1) batch_tile<KK, 1>(im, t, smem);
-  else if (im.ty == 2) batch_tile<KK, 2>(im, t, smem);
+__device__ __forceinline__ void run_tile_k(const BatchArgs& a, const BatchImage& im, int t,
+                                           float* smem) {
+  if (im.ty == 1) batch_tile<KK, 1>(a, im, t, smem);
+  else if (im.ty == 2) batch_tile<KK, 2>(a, im, t, smem);
   else if constexpr (KK <= kBatchMaxK8) {
-    if (im.ty == 8) batch_tile<KK, 8>(im, t, smem);
-    else batch_tile<KK, 4>(im, t, smem);
+    if (im.ty == 8) batch_tile<KK, 8>(a, im, t, smem);
+    else batch_tile<KK, 4>(a, im, t, smem);
   } else {
-    batch_tile<KK, 4>(im, t, smem);
+    batch_tile<KK, 4>(a, im, t, smem);
   }
 }
 
 // One tile of a class-CLS image; a filter side outside the class (a table
 // the host did not split correctly) only raises the status bit.
 template <int CLS>
-__device__ __forceinline__ void run_tile(const BatchImage& im, int t, float* smem,
-                                         unsigned* status) {
+__device__ __forceinline__ void run_tile(const BatchArgs& a, const BatchImage& im, int t,
+                                         float* smem, unsigned* status) {
   switch (im.k) {
 #define CT_BATCH_CASE(KK)                                                        \
   case KK:                                                                       \
     if constexpr (batch_class_of(KK) == CLS) {                                   \
-      run_tile_k<KK>(im, t, smem);                                               \
+      run_tile_k<KK>(a, im, t, smem);                                            \
       return;                                                                    \
     }                                                                            \
     break;
@@ -65,7 +66,7 @@ __host__ __device__ constexpr int batch_class_min_ctas(int cls) { return cls == 
 
 template <int CLS>
 __global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
-    batched_conv_kernel(const BatchArgs a) {
+    batched_conv_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* smem = reinterpret_cast<float*>(smem_raw);
   __shared__ long long s_item;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
       if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
       continue;
     }
-    run_tile<CLS>(im, (int)tl, smem, a.status);  // tiles of one image fit in 32 bits
+    run_tile<CLS>(a, im, (int)tl, smem, a.status);  // tiles of one image fit in 32 bits
   }
 }
 
@@ -146,7 +147,7 @@ int size_class(int h, int w) { return (long long)h * w >= 512LL * 512LL ? 1 : 0;
 
 }  // namespace
 
-int plan_batch(const BatchImage* table, int n, BatchPlan* plan) {
+int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPlan* plan) {
   *plan = BatchPlan();
   int dev = 0, sms = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -176,58 +177,93 @@ int plan_batch(const BatchImage* table, int n, BatchPlan* plan) {
   }
   for (int q = 1; q < n; ++q)
     if (batch_class_of(table[q].k) < batch_class_of(table[q - 1].k)) return CT_EINVAL;
-  int q = 0;
-  for (int c = 0; c < kBatchClasses; ++c) {
-    BatchClassLaunch& L = plan->cls[c];
-    L.lo = q;
-    while (q < n && batch_class_of(table[q].k) == c) {
-      const BatchImage& im = table[q];
-      L.items += (long long)im.tiles_x * im.tiles_y;
-      L.smem = std::max(L.smem, batch_smem_bytes(im.k, im.bx, im.ty));
-      ++q;
+  // Launches: one per class, except that the 13..17 class is cut into runs
+  // whose taps fit one parameter block (the last launches fall back to taps
+  // in shared memory if the counters would run out).
+  auto finish = [&](BatchClassLaunch& L) -> int {
+    L.n = L.hi - L.lo;
+    if (L.n == 0) return CT_OK;
+    size_t buf = 0;
+    for (int q = L.lo; q < L.hi; ++q) {
+      L.items += (long long)table[q].tiles_x * table[q].tiles_y;
+      buf = std::max(buf, batch_smem_bytes(table[q].k, table[q].bx, table[q].ty));
     }
-    L.n = q - L.lo;
-    if (L.n == 0) continue;
     L.item_base = table[L.lo].first_item;
-    L.smem = std::max<size_t>(L.smem, 16);
+    L.smem = std::max<size_t>(buf, 16);
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, batched_kernel_fn(c))) != cudaSuccess)
-      return cuda_status(e);
+    cudaError_t e2 = cudaFuncGetAttributes(&fa, batched_kernel_fn(L.cls));
+    if (e2 != cudaSuccess) return cuda_status(e2);
     if (L.smem + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_fn(c),
-                                                           kBatchThreads, L.smem)) != cudaSuccess)
-      return cuda_status(e);
+    if ((e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_fn(L.cls),
+                                                            kBatchThreads, L.smem)) != cudaSuccess)
+      return cuda_status(e2);
     if (per_sm < 1) return CT_ECONFIG;
     L.grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sms, L.items));
     plan->total_grid += L.grid;
     plan->max_smem = std::max(plan->max_smem, L.smem);
+    plan->launches.push_back(std::move(L));
+    return CT_OK;
+  };
+  int q = 0;
+  for (int c = 0; c < kBatchClasses; ++c) {
+    BatchClassLaunch L;
+    L.cls = c;
+    L.lo = q;
+    int used = 0;  // floats of the parameter block in use
+    for (; q < n && batch_class_of(table[q].k) == c; ++q) {
+      table[q].tap_off = -1;
+      if (c != kBatchClasses - 1 || !host_taps) continue;
+      const int k = table[q].k, kp = (k + 3) / 4 * 4;
+      if (used + k * kp > kBatchParamTaps) {  // this run is full: start the next
+        L.hi = q;
+        int rc = finish(L);
+        if (rc != CT_OK) return rc;
+        L = BatchClassLaunch();
+        L.cls = c;
+        L.lo = q;
+        used = 0;
+      }
+      if ((int)plan->launches.size() + 2 < kBatchMaxLaunches) {
+        table[q].tap_off = used;
+        L.taps.resize(used + k * kp, 0.0f);
+        for (int j = 0; j < k; ++j)
+          for (int i = 0; i < k; ++i) L.taps[used + j * kp + i] = host_taps[q][j * k + i];
+        used += k * kp;
+      }
+    }
+    L.hi = q;
+    int rc = finish(L);
+    if (rc != CT_OK) return rc;
   }
+  if ((int)plan->launches.size() > kBatchMaxLaunches) return CT_ENOTSUP;
   return CT_OK;
 }
 
 int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigned* counters,
                        unsigned* status, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * kBatchClasses, s);
+  const int nl = (int)plan.launches.size();
+  if (nl == 0) return CT_OK;
+  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * nl, s);
   if (e != cudaSuccess) return cuda_status(e);
-  for (int c = 0; c < kBatchClasses; ++c) {
-    const BatchClassLaunch& L = plan.cls[c];
-    if (L.n == 0) continue;
-    BatchArgs a;
+  // the parameter block is copied into the launch (and into a captured graph)
+  static thread_local BatchArgs a;
+  for (int l = 0; l < nl; ++l) {
+    const BatchClassLaunch& L = plan.launches[l];
     a.images = d_table + L.lo;
     a.n_images = L.n;
     a.n_items = L.items;
     a.item_base = L.item_base;
-    a.counter = counters + c;
+    a.counter = counters + l;
     a.status = status;
-    if (c == 0) batched_conv_kernel<0><<<L.grid, kBatchThreads, L.smem, s>>>(a);
-    else if (c == 1) batched_conv_kernel<1><<<L.grid, kBatchThreads, L.smem, s>>>(a);
+    if (!L.taps.empty()) memcpy(a.w, L.taps.data(), sizeof(float) * L.taps.size());
+    if (L.cls == 0) batched_conv_kernel<0><<<L.grid, kBatchThreads, L.smem, s>>>(a);
+    else if (L.cls == 1) batched_conv_kernel<1><<<L.grid, kBatchThreads, L.smem, s>>>(a);
     else batched_conv_kernel<2><<<L.grid, kBatchThreads, L.smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
   }
   return CT_OK;
 }
-
 }  // namespace convtune
 
 using namespace convtune;
@@ -314,6 +350,7 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
       return CT_EINVAL;
     BatchImage im;
     memset(&im, 0, sizeof(im));
+    im.tap_off = -1;
     im.in = it.in;
     im.out = it.out;
     im.in_pitch = it.in_pitch;
@@ -378,6 +415,16 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
                       cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_status(e);
   for (size_t q = 0; q < b->host_images.size(); ++q) b->host_images[q].filt = b->d_filters + offs[q];
+  // persistent grids: resident CTAs per SM x SMs per launch, capped by the
+  // work; the plan also places the 13..17 taps in parameter blocks (it sets
+  // tap_off, so the table goes to the device after it)
+  std::vector<const float*> host_taps(b->host_images.size());
+  for (size_t q = 0; q < b->host_images.size(); ++q) host_taps[q] = b->taps[b->order[q]].data();
+  const int rc = plan_batch(b->host_images.data(), (int)b->host_images.size(), host_taps.data(),
+                            &b->plan);
+  if (rc != CT_OK) return rc;
+  b->grid = b->plan.total_grid;
+  b->smem = std::max<size_t>(b->plan.max_smem, 16);
   const size_t tb = sizeof(BatchImage) * std::max<size_t>(b->host_images.size(), 1);
   if ((e = cudaMalloc(&b->d_images, tb)) != cudaSuccess) return cuda_status(e);
   if (!b->host_images.empty() &&
@@ -385,13 +432,8 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
                       sizeof(BatchImage) * b->host_images.size(), cudaMemcpyHostToDevice)) !=
           cudaSuccess)
     return cuda_status(e);
-  if ((e = cudaMalloc(&b->d_counter, 256)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaMemset(b->d_counter, 0, 256)) != cudaSuccess) return cuda_status(e);
-  // persistent grids: resident CTAs per SM x SMs per class, capped by the work
-  const int rc = plan_batch(b->host_images.data(), (int)b->host_images.size(), &b->plan);
-  if (rc != CT_OK) return rc;
-  b->grid = b->plan.total_grid;
-  b->smem = std::max<size_t>(b->plan.max_smem, 16);
+  if ((e = cudaMalloc(&b->d_counter, kBatchCounterBytes)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemset(b->d_counter, 0, kBatchCounterBytes)) != cudaSuccess) return cuda_status(e);
   return CT_OK;
 }
 
@@ -457,7 +499,7 @@ int ct_batch_info(const ct_batch* b, ct_batch_stats* st) {
   st->grid = b->grid;
   st->smem_bytes = (long)b->smem;
   st->flop = b->flop;
-  for (int c = 0; c < kBatchClasses; ++c) st->launches += b->plan.cls[c].n > 0 ? 1 : 0;
+  st->launches = (int)b->plan.launches.size();
   for (const BatchImage& im : b->host_images)
     st->bytes += 4.0 * ((double)im.in_h * im.in_w + (double)im.out_h * im.out_w + im.k * im.k);
   return CT_OK;
@@ -575,7 +617,7 @@ namespace {
 
 constexpr int kNoAllocMaxImages = 256;
 constexpr int kNoAllocTapFloats = kMaxK * ((kMaxK + 3) / 4 * 4);  // 17 rows of 20
-constexpr size_t kNoAllocHeaderBytes = 256;  // work counter, status word
+constexpr size_t kNoAllocHeaderBytes = kBatchCounterBytes;  // work counters, status word
 constexpr size_t kNoAllocTableBytes = sizeof(BatchImage) * kNoAllocMaxImages;
 constexpr size_t kNoAllocTapBytes = sizeof(float) * (size_t)kNoAllocTapFloats * kNoAllocMaxImages;
 constexpr size_t kNoAllocBytes = kNoAllocHeaderBytes + kNoAllocTableBytes + kNoAllocTapBytes;
@@ -587,7 +629,7 @@ struct NoAllocDevice {
 
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[64];
-// host copy of the image table, per thread (no heap allocation per call)
+// host copy of the image table, per thread
 thread_local BatchImage t_noalloc_table[kNoAllocMaxImages];
 
 }  // namespace
@@ -647,9 +689,9 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   if (m == 0) return CT_OK;
 
   cudaStream_t s = (cudaStream_t)stream;
-  // header: one work counter per filter-side class, then the status word
+  // header: one work counter per launch, the status word in its last word
   unsigned* counters = reinterpret_cast<unsigned*>(nd.base);
-  unsigned* status = counters + kBatchClasses;
+  unsigned* status = counters + kBatchMaxLaunches;
   BatchImage* d_table = reinterpret_cast<BatchImage*>(nd.base + kNoAllocHeaderBytes);
   float* d_taps = reinterpret_cast<float*>(nd.base + kNoAllocHeaderBytes + kNoAllocTableBytes);
   long long first = 0;
@@ -657,6 +699,7 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
     const ct_batch_item& it = items[idx[q]];
     BatchImage& im = t_noalloc_table[q];
     memset(&im, 0, sizeof(im));
+    im.tap_off = -1;
     im.in = it.in;
     im.out = it.out;
     im.in_pitch = it.in_pitch;
@@ -690,15 +733,19 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
                           sizeof(float) * it.k, it.k, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
   }
+  // the plan places the 13..17 taps in parameter blocks (it sets tap_off,
+  // so the table goes to the device after it)
+  const float* host_taps[kNoAllocMaxImages];
+  for (int q = 0; q < m; ++q) host_taps[q] = items[idx[q]].filt;
+  BatchPlan plan;
+  const int rc = plan_batch(t_noalloc_table, m, host_taps, &plan);
+  if (rc != CT_OK) return rc;
   if ((e = cudaMemcpyAsync(d_table, t_noalloc_table, sizeof(BatchImage) * m,
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_status(e);
   // the status word starts clear (the counters are zeroed with the launches)
   if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), s)) != cudaSuccess)
     return cuda_status(e);
-  BatchPlan plan;
-  const int rc = plan_batch(t_noalloc_table, m, &plan);
-  if (rc != CT_OK) return rc;
   return enqueue_batch_plan(plan, d_table, counters, status, s);
 }
 
@@ -714,6 +761,7 @@ int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, 
   if (it.out_h <= 0 || it.out_w <= 0 || !it.in || !it.out) return CT_EINVAL;
   if (it.in_pitch < (long)it.out_w + it.k - 1 || it.out_pitch < it.out_w) return CT_EINVAL;
   memset(im, 0, sizeof(*im));
+  im->tap_off = -1;
   im->in = it.in;
   im->out = it.out;
   im->in_pitch = it.in_pitch;

@@ -28,7 +28,16 @@ struct alignas(16) BatchImage {
   int in_h, in_w, out_h, out_w;
   int k, bx, ty, vw;     // filter side; block_x (block_y = 256 / block_x); tile_y; load width
   int tiles_x, tiles_y;
+  int tap_off;           // >= 0: the taps (K rows of KP floats) start at w[tap_off] of the
+                         // launch's parameter block; -1: read from `filt`
 };
+
+// Floats of taps a launch carries in its parameter block (kernel parameters
+// live in a constant bank: up to 32,764 bytes per launch on this GPU).  The
+// 13..17 class reads its ring taps from there, as the single-image kernel
+// does from its own parameters: a constant-bank operand per FFMA instead of
+// a register filled from shared memory.
+constexpr int kBatchParamTaps = 8000;
 
 struct BatchArgs {
   const BatchImage* images;  // this launch's images (a contiguous run of the table)
@@ -37,7 +46,13 @@ struct BatchArgs {
   long long item_base;       // first_item of images[0]: item w is table item item_base + w
   unsigned* counter;         // work counter, zero at launch
   unsigned* status;          // device status word
+  alignas(16) float w[kBatchParamTaps];  // taps of the images with tap_off >= 0
 };
+static_assert(sizeof(BatchArgs) <= 32764, "kernel parameter block too large");
+
+// Work counters (one per launch of a batch) live in a 1 KB region.
+constexpr int kBatchCounterBytes = 1024;
+constexpr int kBatchMaxLaunches = kBatchCounterBytes / 4 - 1;  // one word left for a status
 
 // Filter sides are split into classes, one persistent kernel each: a kernel's
 // register allocation is that of its largest body, and the small-filter
@@ -55,7 +70,8 @@ struct BatchStage {
 };
 
 template <int K, int TY>
-__device__ __forceinline__ void batch_tile(const BatchImage& im, int t, float* smem) {
+__device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage& im, int t,
+                                           float* smem) {
   constexpr int TX = kBatchTileX;
   constexpr int KP = (K + 3) / 4 * 4;
   constexpr int kFilt = (K * KP + 31) / 32 * 32;
@@ -75,7 +91,9 @@ __device__ __forceinline__ void batch_tile(const BatchImage& im, int t, float* s
   st.tile_w = (bx * TX + K - 1 + 3) / 4 * 4;
   st.tile_h = by * TY + K - 1;
   st.smem_pitch = st.tile_w;
-  for (int q = tid; q < K * KP; q += kBatchThreads) sfilt[q] = im.filt[q];
+  const bool param_taps = uses_ring(K, TX, TY) && im.tap_off >= 0;  // CTA-uniform
+  if (!param_taps)
+    for (int q = tid; q < K * KP; q += kBatchThreads) sfilt[q] = im.filt[q];
   stage_tile_cp_async(st, tile, gx0, gy0);
   __syncthreads();
 
@@ -86,18 +104,30 @@ __device__ __forceinline__ void batch_tile(const BatchImage& im, int t, float* s
   // matters even more); taps come from shared memory, so the loop keeps its
   // bounds tests (the peeled form needs 128 registers and a stack frame here)
   if constexpr (uses_ring(K, TX, TY)) {
-    accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
-        acc, [&](int r) { return sbase + r * st.smem_pitch; },
-        [&](int j, float(&w)[KP]) {
+    if (param_taps) {
+      // taps from the parameter block (constant bank), as in the single-image
+      // kernel's ring
+      const float* wrow = a.w + im.tap_off;
+      accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
+          acc, [&](int r) { return sbase + r * st.smem_pitch; },
+          [&](int j, float(&w)[KP]) {
 #pragma unroll
-          for (int i = 0; i < KP; i += 4) {
-            const float4 q = *reinterpret_cast<const float4*>(sfilt + j * KP + i);
-            w[i] = q.x;
-            w[i + 1] = q.y;
-            w[i + 2] = q.z;
-            w[i + 3] = q.w;
-          }
-        });
+            for (int i = 0; i < K; ++i) w[i] = wrow[j * KP + i];
+          });
+    } else {
+      accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
+          acc, [&](int r) { return sbase + r * st.smem_pitch; },
+          [&](int j, float(&w)[KP]) {
+#pragma unroll
+            for (int i = 0; i < KP; i += 4) {
+              const float4 q = *reinterpret_cast<const float4*>(sfilt + j * KP + i);
+              w[i] = q.x;
+              w[i + 1] = q.y;
+              w[i + 2] = q.z;
+              w[i + 3] = q.w;
+            }
+          });
+    }
   } else {
     accumulate_tile<K, TX, TY>(
         acc,

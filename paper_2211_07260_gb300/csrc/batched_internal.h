@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include "../../include/convtune.h"
+#include <vector>
+
 #include "batched.cuh"
 
 namespace convtune {
@@ -14,28 +16,34 @@ namespace convtune {
 int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, BatchImage* im,
                           size_t* smem);
 
-// Launch plan of a host copy of a batch table: the table must be ordered by
-// filter-side class (batch_class_of, ascending); each class's contiguous run
-// of images gets its own persistent kernel, with that run's shared memory and
-// an occupancy-sized grid.  The first call per device raises the class
-// kernels' shared-memory caps (make it before any stream capture).
+// Launch plan of a host copy of a batch table, which must be ordered by
+// filter-side class (batch_class_of, ascending).  Each class's contiguous run
+// of images gets a persistent kernel with that run's shared memory and an
+// occupancy-sized grid; the 13..17 class is cut into runs whose taps
+// (host_taps[q]: k x k row-major, host) fit one launch's parameter block.
+// The plan sets each entry's tap_off, so copy the table to the device after
+// planning.  host_taps may be NULL (taps then come from shared memory).  The
+// first call per device raises the class kernels' shared-memory caps (make
+// it before any stream capture).
 struct BatchClassLaunch {
-  int lo = 0, n = 0;          // run of the table
+  int cls = 0;                // filter-side class
+  int lo = 0, hi = 0, n = 0;  // run of the table
   long long items = 0;        // work items of the run
   long long item_base = 0;    // first_item of its first image
   size_t smem = 0;            // dynamic shared memory per CTA
   int grid = 0;               // persistent CTAs
+  std::vector<float> taps;    // the run's parameter-block taps (KP-padded rows)
 };
 struct BatchPlan {
-  BatchClassLaunch cls[kBatchClasses];
+  std::vector<BatchClassLaunch> launches;
   int total_grid = 0;
   size_t max_smem = 0;
 };
-int plan_batch(const BatchImage* table, int n, BatchPlan* plan);
+int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPlan* plan);
 
-// Enqueue a planned batch over the device copy of the same table: zeroes the
-// kBatchClasses work counters at `counters`, then launches the class kernels
-// one after another on `s`.
+// Enqueue a planned batch over the device copy of the same table: zeroes one
+// work counter per launch at `counters` (kBatchCounterBytes of device
+// memory), then launches the kernels one after another on `s`.
 int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigned* counters,
                        unsigned* status, cudaStream_t s);
 

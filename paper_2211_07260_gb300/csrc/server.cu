@@ -228,6 +228,12 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
       first += (long long)im.tiles_x * im.tiles_y;
     }
     const size_t n = batch.size();
+    // the plan places the 13..17 taps in parameter blocks and sets tap_off:
+    // the table goes to the device after it
+    std::vector<const float*> host_taps(n);
+    for (size_t q = 0; q < n; ++q) host_taps[q] = batch[q]->taps;
+    BatchPlan plan;
+    if ((rc = plan_batch(sl.h_table, (int)n, host_taps.data(), &plan)) != CT_OK) return rc;
     if ((e = cudaMemcpyAsync(sl.d_taps, sl.h_taps, sizeof(float) * kTapFloats * n,
                              cudaMemcpyHostToDevice, sl.s)) != cudaSuccess)
       return cuda_status(e);
@@ -237,8 +243,6 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
     int err = CT_OK;
     unsigned* status = device_status_word(&err);
     if (!status) return err;
-    BatchPlan plan;
-    if ((rc = plan_batch(sl.h_table, (int)n, &plan)) != CT_OK) return rc;
     if ((rc = enqueue_batch_plan(plan, sl.d_table, sl.d_counter, status, sl.s)) != CT_OK)
       return rc;
   }
@@ -389,7 +393,8 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
   sv->alloc = new PoolAlloc(sv->pool_bytes);
   const size_t per_slot_table = sizeof(BatchImage) * opt->max_batch;
   const size_t per_slot_taps = sizeof(float) * kTapFloats * opt->max_batch;
-  const size_t per_slot = (per_slot_table + per_slot_taps + 256 + kAlign - 1) / kAlign * kAlign;
+  const size_t per_slot =
+      (per_slot_table + per_slot_taps + kBatchCounterBytes + kAlign - 1) / kAlign * kAlign;
   if ((e = cudaMalloc(&sv->slot_mem, per_slot * opt->n_streams)) != cudaSuccess) {
     delete sv;
     return cuda_status(e);
@@ -398,9 +403,9 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
   for (int i = 0; i < opt->n_streams; ++i) {
     Slot& sl = sv->slots[i];
     unsigned char* base = sv->slot_mem + per_slot * i;
-    sl.d_counter = reinterpret_cast<unsigned*>(base);
-    sl.d_table = reinterpret_cast<BatchImage*>(base + 256);
-    sl.d_taps = reinterpret_cast<float*>(base + 256 + per_slot_table);
+    sl.d_counter = reinterpret_cast<unsigned*>(base);  // one work counter per launch
+    sl.d_table = reinterpret_cast<BatchImage*>(base + kBatchCounterBytes);
+    sl.d_taps = reinterpret_cast<float*>(base + kBatchCounterBytes + per_slot_table);
     if ((e = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMallocHost(&sl.h_table, per_slot_table)) != cudaSuccess ||
@@ -415,7 +420,7 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
   // ~40 ms stalls measured at 5000 requests/s; batched: the class kernels).
   {
     BatchPlan warm;
-    int rc = plan_batch(nullptr, 0, &warm);
+    int rc = plan_batch(nullptr, 0, nullptr, &warm);
     for (int k = 1; rc == CT_OK && opt->plain && k <= kMaxK; k += 2)
       for (int cls = 0; rc == CT_OK && cls < 2; ++cls) {
         ct_batch_item it;
