@@ -241,15 +241,25 @@ int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPla
 }
 
 int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigned* counters,
-                       unsigned* status, cudaStream_t s) {
+                       unsigned* status, cudaStream_t s, const cudaStream_t* branches,
+                       const cudaEvent_t* events, int n_branches) {
   const int nl = (int)plan.launches.size();
   if (nl == 0) return CT_OK;
   cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * nl, s);
   if (e != cudaSuccess) return cuda_status(e);
+  // launch l runs on branch l (when given): s forks after the counter reset
+  // and joins every branch at the end
+  const bool fork = branches && events && n_branches >= nl;
+  if (fork && (e = cudaEventRecord(events[nl], s)) != cudaSuccess) return cuda_status(e);
   // the parameter block is copied into the launch (and into a captured graph)
   static thread_local BatchArgs a;
   for (int l = 0; l < nl; ++l) {
     const BatchClassLaunch& L = plan.launches[l];
+    cudaStream_t ls = s;
+    if (fork) {
+      ls = branches[l];
+      if ((e = cudaStreamWaitEvent(ls, events[nl], 0)) != cudaSuccess) return cuda_status(e);
+    }
     a.images = d_table + L.lo;
     a.n_images = L.n;
     a.n_items = L.items;
@@ -257,10 +267,13 @@ int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigne
     a.counter = counters + l;
     a.status = status;
     if (!L.taps.empty()) memcpy(a.w, L.taps.data(), sizeof(float) * L.taps.size());
-    if (L.cls == 0) batched_conv_kernel<0><<<L.grid, kBatchThreads, L.smem, s>>>(a);
-    else if (L.cls == 1) batched_conv_kernel<1><<<L.grid, kBatchThreads, L.smem, s>>>(a);
-    else batched_conv_kernel<2><<<L.grid, kBatchThreads, L.smem, s>>>(a);
+    if (L.cls == 0) batched_conv_kernel<0><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
+    else if (L.cls == 1) batched_conv_kernel<1><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
+    else batched_conv_kernel<2><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    if (fork && ((e = cudaEventRecord(events[l], ls)) != cudaSuccess ||
+                 (e = cudaStreamWaitEvent(s, events[l], 0)) != cudaSuccess))
+      return cuda_status(e);
   }
   return CT_OK;
 }
@@ -284,8 +297,14 @@ struct ct_batch {
   double flop = 0;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture_stream = nullptr;
+  // branches of the captured graph: one stream per launch, so that one
+  // launch's last tiles overlap the next launch's first ones
+  std::vector<cudaStream_t> branches;
+  std::vector<cudaEvent_t> events;  // one per launch + the fork
   ~ct_batch() {
     if (exec) cudaGraphExecDestroy(exec);
+    for (cudaStream_t bs : branches) cudaStreamDestroy(bs);
+    for (cudaEvent_t ev : events) cudaEventDestroy(ev);
     if (capture_stream) cudaStreamDestroy(capture_stream);
     if (d_images) cudaFree(d_images);
     if (d_filters) cudaFree(d_filters);
@@ -301,7 +320,10 @@ int enqueue_batch(ct_batch* b, cudaStream_t s) {
   int err = CT_OK;
   unsigned* status = device_status_word(&err);
   if (!status) return err;
-  return enqueue_batch_plan(b->plan, b->d_images, b->d_counter, status, s);
+  return enqueue_batch_plan(b->plan, b->d_images, b->d_counter, status, s,
+                            b->branches.empty() ? nullptr : b->branches.data(),
+                            b->events.empty() ? nullptr : b->events.data(),
+                            (int)b->branches.size());
 }
 
 // The plain comparison: one ct_conv2d_run per image, configuration from the
@@ -443,6 +465,19 @@ int capture_batch(ct_batch* b) {
   if (!device_status_word(&err)) return err;
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_status(e);
+  const size_t nl = b->plan.launches.size();
+  for (size_t l = 0; l < nl; ++l) {
+    cudaStream_t bs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_status(e);
+    b->branches.push_back(bs);
+  }
+  for (size_t l = 0; l <= nl; ++l) {
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_status(e);
+    b->events.push_back(ev);
+  }
   if ((e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal)) !=
       cudaSuccess)
     return cuda_status(e);
