@@ -177,9 +177,9 @@ int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPla
   }
   for (int q = 1; q < n; ++q)
     if (batch_class_of(table[q].k) < batch_class_of(table[q - 1].k)) return CT_EINVAL;
-  // Launches: one per class, except that the 13..17 class is cut into runs
-  // whose taps fit one parameter block (the last launches fall back to taps
-  // in shared memory if the counters would run out).
+  // Launches: one per class, cut into runs whose taps fit one parameter
+  // block (the last launches fall back to taps in shared memory if the
+  // counters would run out).
   auto finish = [&](BatchClassLaunch& L) -> int {
     L.n = L.hi - L.lo;
     if (L.n == 0) return CT_OK;
@@ -213,7 +213,7 @@ int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPla
     int used = 0;  // floats of the parameter block in use
     for (; q < n && batch_class_of(table[q].k) == c; ++q) {
       table[q].tap_off = -1;
-      if (c != kBatchClasses - 1 || !host_taps) continue;
+      if (!host_taps) continue;
       const int k = table[q].k, kp = (k + 3) / 4 * 4;
       if (used + k * kp > kBatchParamTaps) {  // this run is full: start the next
         L.hi = q;

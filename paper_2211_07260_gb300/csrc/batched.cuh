@@ -91,7 +91,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage&
   st.tile_w = (bx * TX + K - 1 + 3) / 4 * 4;
   st.tile_h = by * TY + K - 1;
   st.smem_pitch = st.tile_w;
-  const bool param_taps = uses_ring(K, TX, TY) && im.tap_off >= 0;  // CTA-uniform
+  const bool param_taps = im.tap_off >= 0;  // CTA-uniform
   if (!param_taps)
     for (int q = tid; q < K * KP; q += kBatchThreads) sfilt[q] = im.filt[q];
   stage_tile_cp_async(st, tile, gx0, gy0);
@@ -128,6 +128,12 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage&
             }
           });
     }
+  } else if (param_taps) {
+    const float* wp = a.w + im.tap_off;
+    accumulate_tile<K, TX, TY>(
+        acc,
+        [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
+        [&](int j, int i) -> float { return wp[j * KP + i]; });
   } else {
     accumulate_tile<K, TX, TY>(
         acc,
