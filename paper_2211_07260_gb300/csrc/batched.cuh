@@ -33,10 +33,12 @@ struct alignas(16) BatchImage {
 };
 
 // Floats of taps a launch carries in its parameter block (kernel parameters
-// live in a constant bank: up to 32,764 bytes per launch on this GPU).  The
-// 13..17 class reads its ring taps from there, as the single-image kernel
-// does from its own parameters: a constant-bank operand per FFMA instead of
-// a register filled from shared memory.
+// live in a constant bank: up to 32,764 bytes per launch on this GPU).  Tiles
+// read their image's taps from there, as the single-image kernel does from
+// its own parameters, instead of from a shared-memory copy (GB300, 256-image
+// batch: filter sides 5..15 5-9 % faster); a launch holds the images whose
+// taps fit, and taps in shared memory remain for images beyond the launches
+// a batch may have.
 constexpr int kBatchParamTaps = 8000;
 
 struct BatchArgs {
@@ -101,8 +103,9 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage&
   const float* sbase = tile + (ly * TY) * st.smem_pitch + lx * TX;
   // large bodies take the ring form, as in the single-image kernel (this
   // kernel holds one body per filter side and tile height, so its code size
-  // matters even more); taps come from shared memory, so the loop keeps its
-  // bounds tests (the peeled form needs 128 registers and a stack frame here)
+  // matters even more); the loop keeps its bounds tests here (the peeled
+  // form measured slower with parameter taps, and needs 128 registers and a
+  // stack frame with shared-memory taps)
   if constexpr (uses_ring(K, TX, TY)) {
     if (param_taps) {
       // taps from the parameter block (constant bank), as in the single-image
