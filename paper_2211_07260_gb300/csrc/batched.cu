@@ -127,6 +127,8 @@ const void* batched_kernel_fn(int cls) {
 
 namespace {
 
+constexpr size_t kBatchBranches = 8;  // parallel branches of a captured batch graph
+
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 size_t batch_smem_bytes(int k, int bx, int ty) {
@@ -247,19 +249,18 @@ int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigne
   if (nl == 0) return CT_OK;
   cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * nl, s);
   if (e != cudaSuccess) return cuda_status(e);
-  // launch l runs on branch l (when given): s forks after the counter reset
-  // and joins every branch at the end
-  const bool fork = branches && events && n_branches >= nl;
-  if (fork && (e = cudaEventRecord(events[nl], s)) != cudaSuccess) return cuda_status(e);
+  // launch l runs on branch l % n_branches (when given): s forks after the
+  // counter reset and joins every branch at the end
+  const int nb = (branches && events) ? std::min(n_branches, nl) : 0;
+  if (nb > 0 && (e = cudaEventRecord(events[nb], s)) != cudaSuccess) return cuda_status(e);
+  for (int b = 0; b < nb; ++b)
+    if ((e = cudaStreamWaitEvent(branches[b], events[nb], 0)) != cudaSuccess)
+      return cuda_status(e);
   // the parameter block is copied into the launch (and into a captured graph)
   static thread_local BatchArgs a;
   for (int l = 0; l < nl; ++l) {
     const BatchClassLaunch& L = plan.launches[l];
-    cudaStream_t ls = s;
-    if (fork) {
-      ls = branches[l];
-      if ((e = cudaStreamWaitEvent(ls, events[nl], 0)) != cudaSuccess) return cuda_status(e);
-    }
+    const cudaStream_t ls = nb > 0 ? branches[l % nb] : s;
     a.images = d_table + L.lo;
     a.n_images = L.n;
     a.n_items = L.items;
@@ -271,10 +272,11 @@ int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigne
     else if (L.cls == 1) batched_conv_kernel<1><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
     else batched_conv_kernel<2><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    if (fork && ((e = cudaEventRecord(events[l], ls)) != cudaSuccess ||
-                 (e = cudaStreamWaitEvent(s, events[l], 0)) != cudaSuccess))
-      return cuda_status(e);
   }
+  for (int b = 0; b < nb; ++b)
+    if ((e = cudaEventRecord(events[b], branches[b])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, events[b], 0)) != cudaSuccess)
+      return cuda_status(e);
   return CT_OK;
 }
 }  // namespace convtune
@@ -297,10 +299,10 @@ struct ct_batch {
   double flop = 0;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture_stream = nullptr;
-  // branches of the captured graph: one stream per launch, so that one
-  // launch's last tiles overlap the next launch's first ones
+  // branches of the captured graph (launch l on branch l % kBatchBranches),
+  // so that one launch's last tiles overlap the next launch's first ones
   std::vector<cudaStream_t> branches;
-  std::vector<cudaEvent_t> events;  // one per launch + the fork
+  std::vector<cudaEvent_t> events;  // one per branch + the fork
   ~ct_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     for (cudaStream_t bs : branches) cudaStreamDestroy(bs);
@@ -465,7 +467,7 @@ int capture_batch(ct_batch* b) {
   if (!device_status_word(&err)) return err;
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_status(e);
-  const size_t nl = b->plan.launches.size();
+  const size_t nl = std::min<size_t>(b->plan.launches.size(), kBatchBranches);
   for (size_t l = 0; l < nl; ++l) {
     cudaStream_t bs = nullptr;
     if ((e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) != cudaSuccess)

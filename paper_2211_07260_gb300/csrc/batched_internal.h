@@ -44,8 +44,8 @@ int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPla
 // Enqueue a planned batch over the device copy of the same table: zeroes one
 // work counter per launch at `counters` (kBatchCounterBytes of device
 // memory), then launches the kernels one after another on `s` or, with
-// branch streams (one per launch) and events (one per launch + 1), each on
-// its own branch forked from and joined back into `s`.
+// n_branches branch streams and n_branches + 1 events, launch l on branch
+// l % n_branches, the branches forked from and joined back into `s`.
 int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigned* counters,
                        unsigned* status, cudaStream_t s, const cudaStream_t* branches = nullptr,
                        const cudaEvent_t* events = nullptr, int n_branches = 0);

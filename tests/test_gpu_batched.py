@@ -115,3 +115,26 @@ def test_bucket_tuning_and_measurement():
     torch.cuda.synchronize()
     for p, o in zip(probs, outs):
         assert max_rel_err(o.cpu().numpy()[:, :p.out_w], oracle_ref(p)) <= MAX_REL
+
+
+def test_many_images_fill_every_parameter_block_then_fall_back():
+    # 6000 one-output 17x17 images: their taps fill a parameter block every
+    # 23 images, so the launches run out (254 per batch) and the last images
+    # read their taps from shared memory; 8 graph branches carry the
+    # launches.  Every output still equals the plain launch, bit for bit.
+    n = 6000
+    probs = [synth.conv_problem(1, 1, 17, seed=[11, i]) for i in range(n)]
+    ents, outs = device_entries(probs)
+    ents_p, outs_p = device_entries(probs)
+    with api.Batch(ents, None) as b, api.Batch(ents_p, None) as bp:
+        st = b.info()
+        assert st["launches"] == 254
+        b.run()
+        bp.run_plain()
+        torch.cuda.synchronize()
+        got = torch.stack([o[:, :1] for o in outs]).cpu().numpy()
+        ref = torch.stack([o[:, :1] for o in outs_p]).cpu().numpy()
+    assert np.array_equal(got, ref)
+    taps_sum = np.array([float((p.inp[:17, :17].astype(np.float64) * p.filt).sum()) for p in probs])
+    assert np.max(np.abs(got.ravel() - taps_sum) / np.abs(taps_sum)) <= MAX_REL
+    assert api.status_read(clear=True) == 0
