@@ -556,13 +556,16 @@ int ct_batch_run_noalloc(const ct_batch_item* items, int n, const ct_batch_tiles
  * time from any thread.  A worker thread admits them in arrival order while
  * a device-resident pool (allocated at creation, at most 90 % of the free
  * device memory) has room for their buffers, and dispatches admitted
- * requests as batches on up to n_streams streams at once: copy in, one
- * persistent batched launch (or, with `plain`, one plain launch per
- * request), copy out.  A batch leaves when it is full, when no batch is in
- * flight, or when its oldest request has waited max_wait_s; requests that
- * arrive while others run join the next batch.  Results are bitwise equal to
- * a request served alone.  Latency = submission to completion seen by the
- * worker.  Host buffers must stay valid until the request completes.
+ * requests as batches on up to n_streams streams at once: copy in, the
+ * persistent batched kernels (one per filter-side class present; or, with
+ * `plain`, one plain launch per request), copy out.  A batch leaves when it
+ * is full, when no batch is in flight, or when its oldest request has
+ * waited max_wait_s; requests that arrive while others run join the next
+ * batch.  Results are bitwise equal to a request served alone.  Latency =
+ * submission to completion seen by the worker.  Host buffers must stay
+ * valid until the request completes.  Creation also loads every kernel the
+ * worker can launch (kernel code is otherwise loaded on first use, which
+ * would stall the worker with requests queued behind it).
  */
 typedef struct {
   int n_streams;         /* batches in flight at once, 1..64                */
