@@ -136,7 +136,7 @@ size_t batch_smem_bytes(int k, int bx, int ty) {
   const int filt = round_up(k * kp, 32);
   const int by = kBatchThreads / bx;
   const int tile_w = round_up(bx * kBatchTileX + k - 1, 4);
-  const int tile_h = by * ty + k - 1;
+  const int tile_h = batch_subtiles(k) * by * ty + k - 1;
   return sizeof(float) * (size_t)(filt + tile_w * tile_h);
 }
 
@@ -396,7 +396,7 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
                          (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
     im.vw = aligned ? 4 : 1;
     im.tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
-    im.tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
+    im.tiles_y = (it.out_h + batch_item_rows(it.k, bx, ty) - 1) / batch_item_rows(it.k, bx, ty);
     imgs.push_back(im);
     order.push_back(i);
     b->flop += 2.0 * it.k * it.k * (double)it.out_h * it.out_w;
@@ -758,7 +758,7 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
                          (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
     im.vw = aligned ? 4 : 1;
     im.tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
-    im.tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
+    im.tiles_y = (it.out_h + batch_item_rows(it.k, bx, ty) - 1) / batch_item_rows(it.k, bx, ty);
     im.first_item = first;
     first += (long long)im.tiles_x * im.tiles_y;
     // taps: k rows padded to round_up(k, 4) floats (the padding is never used
@@ -820,7 +820,7 @@ int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, 
                        (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
   im->vw = aligned ? 4 : 1;
   im->tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
-  im->tiles_y = (it.out_h + (kBatchThreads / bx) * ty - 1) / ((kBatchThreads / bx) * ty);
+  im->tiles_y = (it.out_h + batch_item_rows(it.k, bx, ty) - 1) / batch_item_rows(it.k, bx, ty);
   *smem = std::max(*smem, batch_smem_bytes(it.k, bx, ty));
   return CT_OK;
 }

@@ -64,6 +64,16 @@ constexpr int kBatchMaxLaunches = kBatchCounterBytes / 4 - 1;  // one word left 
 constexpr int kBatchClasses = 3;
 __host__ __device__ constexpr int batch_class_of(int k) { return k <= 7 ? 0 : (k <= 11 ? 1 : 2); }
 
+// Vertically adjacent tiles per work item: the 13..17 class stages one block
+// for two tiles (half the stage / barrier cycles per output, and the K-1
+// halo rows shared between the two) and computes them one after the other.
+__host__ __device__ constexpr int batch_subtiles(int k) { return batch_class_of(k) == 2 ? 2 : 1; }
+
+// Output rows one work item covers.
+__host__ __device__ constexpr int batch_item_rows(int k, int bx, int ty) {
+  return batch_subtiles(k) * (kBatchThreads / bx) * ty;
+}
+
 // Fields stage_tile_cp_async() reads.
 struct BatchStage {
   const float* in;
@@ -81,7 +91,8 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage&
   const int tid = threadIdx.x;
   const int lx = tid % bx, ly = tid / bx;
   const int ti = t % im.tiles_x, tj = t / im.tiles_x;
-  const int gx0 = ti * bx * TX, gy0 = tj * by * TY;
+  constexpr int SUB = batch_subtiles(K);
+  const int gx0 = ti * bx * TX, gy0 = tj * SUB * by * TY;
   float* sfilt = smem;
   float* tile = smem + kFilt;
   BatchStage st;
@@ -91,7 +102,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage&
   st.in_w = im.in_w;
   st.vw = im.vw;
   st.tile_w = (bx * TX + K - 1 + 3) / 4 * 4;
-  st.tile_h = by * TY + K - 1;
+  st.tile_h = SUB * by * TY + K - 1;
   st.smem_pitch = st.tile_w;
   const bool param_taps = im.tap_off >= 0;  // CTA-uniform
   if (!param_taps)
@@ -99,55 +110,59 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage&
   stage_tile_cp_async(st, tile, gx0, gy0);
   __syncthreads();
 
-  float acc[TY][TX];
-  const float* sbase = tile + (ly * TY) * st.smem_pitch + lx * TX;
-  // large bodies take the ring form, as in the single-image kernel (this
-  // kernel holds one body per filter side and tile height, so its code size
-  // matters even more); the loop keeps its bounds tests here (the peeled
-  // form measured slower with parameter taps, and needs 128 registers and a
-  // stack frame with shared-memory taps)
-  if constexpr (uses_ring(K, TX, TY)) {
-    if (param_taps) {
-      // taps from the parameter block (constant bank), as in the single-image
-      // kernel's ring
-      const float* wrow = a.w + im.tap_off;
-      accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
-          acc, [&](int r) { return sbase + r * st.smem_pitch; },
-          [&](int j, float(&w)[KP]) {
+  // the item's SUB tiles, one after the other, from the one staged block
+#pragma unroll 1
+  for (int sub = 0; sub < SUB; ++sub) {
+    float acc[TY][TX];
+    const float* sbase = tile + (sub * by * TY + ly * TY) * st.smem_pitch + lx * TX;
+    // large bodies take the ring form, as in the single-image kernel (this
+    // kernel holds one body per filter side and tile height, so its code size
+    // matters even more); the loop keeps its bounds tests here (the peeled
+    // form measured slower with parameter taps, and needs 128 registers and a
+    // stack frame with shared-memory taps)
+    if constexpr (uses_ring(K, TX, TY)) {
+      if (param_taps) {
+        // taps from the parameter block (constant bank), as in the single-image
+        // kernel's ring
+        const float* wrow = a.w + im.tap_off;
+        accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
+            acc, [&](int r) { return sbase + r * st.smem_pitch; },
+            [&](int j, float(&w)[KP]) {
 #pragma unroll
-            for (int i = 0; i < K; ++i) w[i] = wrow[j * KP + i];
-          });
+              for (int i = 0; i < K; ++i) w[i] = wrow[j * KP + i];
+            });
+      } else {
+        accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
+            acc, [&](int r) { return sbase + r * st.smem_pitch; },
+            [&](int j, float(&w)[KP]) {
+#pragma unroll
+              for (int i = 0; i < KP; i += 4) {
+                const float4 q = *reinterpret_cast<const float4*>(sfilt + j * KP + i);
+                w[i] = q.x;
+                w[i + 1] = q.y;
+                w[i + 2] = q.z;
+                w[i + 3] = q.w;
+              }
+            });
+      }
+    } else if (param_taps) {
+      const float* wp = a.w + im.tap_off;
+      accumulate_tile<K, TX, TY>(
+          acc,
+          [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
+          [&](int j, int i) -> float { return wp[j * KP + i]; });
     } else {
-      accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
-          acc, [&](int r) { return sbase + r * st.smem_pitch; },
-          [&](int j, float(&w)[KP]) {
-#pragma unroll
-            for (int i = 0; i < KP; i += 4) {
-              const float4 q = *reinterpret_cast<const float4*>(sfilt + j * KP + i);
-              w[i] = q.x;
-              w[i + 1] = q.y;
-              w[i + 2] = q.z;
-              w[i + 3] = q.w;
-            }
-          });
+      accumulate_tile<K, TX, TY>(
+          acc,
+          [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
+          [&](int j, int i) -> float { return sfilt[j * KP + i]; });
     }
-  } else if (param_taps) {
-    const float* wp = a.w + im.tap_off;
-    accumulate_tile<K, TX, TY>(
-        acc,
-        [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
-        [&](int j, int i) -> float { return wp[j * KP + i]; });
-  } else {
-    accumulate_tile<K, TX, TY>(
-        acc,
-        [&](int r, float(&rowv)[TX + K - 1]) { fetch_row_smem<K, TX>(rowv, sbase + r * st.smem_pitch); },
-        [&](int j, int i) -> float { return sfilt[j * KP + i]; });
-  }
-  const int x0 = gx0 + lx * TX, y0 = gy0 + ly * TY;
+    const int x0 = gx0 + lx * TX, y0 = gy0 + sub * by * TY + ly * TY;
 #pragma unroll
-  for (int r = 0; r < TY; ++r) {
-    const int y = y0 + r;
-    if (y < im.out_h) store_run<TX>(im.out + (long long)y * im.out_pitch, x0, im.out_w, im.vw, acc[r]);
+    for (int r = 0; r < TY; ++r) {
+      const int y = y0 + r;
+      if (y < im.out_h) store_run<TX>(im.out + (long long)y * im.out_pitch, x0, im.out_w, im.vw, acc[r]);
+    }
   }
   __syncthreads();  // the next item reuses the shared memory
 }
