@@ -349,6 +349,64 @@ int ct_pick_clock_range(const ct_power_model* m, const int* supported_mhz, int n
                         double rel_halfwidth, int center, int* out_mhz, int cap, int* n_out,
                         double* center_mhz);
 
+/* ---- memory-aware energy model (Sections II and IV-F) ------------------- */
+
+/*
+ * Section IV-E estimates energy as P*(f)/f, i.e. run time ~ 1/f: right for
+ * compute-bound kernels.  Section IV-F plans memory-dependent terms (the
+ * estimate sometimes misses the measured optimum) and Section II recalls the
+ * roofline energy model of Choi et al., where memory traffic costs energy
+ * that compute cannot hide.  The paper gives no formula; this library reads
+ * it as a run time with a clock-independent memory part,
+ *
+ *   t(f) = t_mem + c_core / f      (f in GHz; t_mem, c_core >= 0),
+ *
+ * fitted by non-negative linear least squares to a unit's (clock, time)
+ * samples (throttled samples dropped), and energy per unit
+ *
+ *   E(f) = P*(f) * t(f),
+ *
+ * with P*(f) of Eq. powercurve fitted on the same unit's power samples.  For
+ * t_mem = 0 this is the paper's estimate.  The stream-copy microbenchmark
+ * (CT_UNIT_COPY) gives the memory-bound curve.
+ */
+typedef struct {
+  double t_mem_s;        /* clock-independent time per unit (s)             */
+  double c_core_s_ghz;   /* clock-bound time per unit at 1 GHz (s GHz)      */
+  double sse;            /* residual sum of squares of the kept samples     */
+  int n_used;            /* samples kept (not throttled)                    */
+  double f_lo_mhz;       /* lowest kept sample clock                        */
+  double f_thr_mhz;      /* highest kept sample clock                       */
+} ct_time_model;
+
+/*
+ * Fit t(f) to n >= 2 samples (clocks in MHz > 0, times in s, throttled
+ * optional): the unconstrained least-squares line in (1, 1/f) when both
+ * coefficients are >= 0, else the better of the fits with t_mem = 0 or
+ * c_core = 0 (each clamped at 0).  CT_EINVAL on bad input or fewer than two
+ * kept samples.
+ */
+int ct_fit_time_model(const double* f_mhz, const double* t_s, const int* throttled_or_null,
+                      int n, ct_time_model* out);
+/* t(f) at n clocks (MHz). */
+int ct_model_time(const ct_time_model* tm, const double* f_mhz, int n, double* t_s);
+/*
+ * Memory-aware optimum: the integer-MHz clock minimising P*(f) t(f) over
+ * [max(pm.f_lo, tm.f_lo), min(pm.f_thr, tm.f_thr)] (ties: lower clock);
+ * *e_opt_j (optional) receives E there.  The power model must be an
+ * estimated-voltage fit (CT_EINVAL otherwise, or if the range holds no
+ * integer clock).
+ */
+int ct_memory_aware_optimum(const ct_power_model* pm, const ct_time_model* tm,
+                            double* f_opt_mhz, double* e_opt_j);
+/*
+ * Supported clocks within +-rel_halfwidth of center_mhz, ascending (the
+ * +-10 % rule of Section IV-E around any centre); an empty window yields the
+ * nearest supported clock (ties: lower).  CT_ENOMEM if *n_out exceeds cap.
+ */
+int ct_clock_range(double center_mhz, const int* supported_mhz, int n_supported,
+                   double rel_halfwidth, int* out_mhz, int cap, int* n_out);
+
 /* ---- tuning (Sections III-C and IV) ------------------------------------- */
 
 enum { CT_OBJ_TIME = 0, CT_OBJ_ENERGY = 1, CT_OBJ_GFLOPS_PER_W = 2 };
@@ -423,20 +481,35 @@ int ct_microbench_release(void);
 
 /* Result of the model-steered search. */
 typedef struct {
-  ct_power_model model;  /* fitted on the microbenchmark sweep              */
-  double center_mhz;     /* model optimum the clock range is centred on     */
+  ct_power_model model;  /* the model the range is centred on (see below)   */
+  double center_mhz;     /* its optimum                                     */
   int n_range;           /* clocks in the steered range                     */
-  double fit_wall_s;     /* host seconds: microbenchmark sweep + fit        */
+  double fit_wall_s;     /* host seconds: microbenchmark sweeps + fits      */
   double tune_wall_s;    /* host seconds: the steered sweep                 */
+  ct_power_model model_mem;  /* stream-copy power fit (CT_UNIT_COPY, union) */
+  ct_time_model time_mem;    /* stream-copy time fit                        */
+  double center_mem_mhz;     /* memory-aware optimum of the two             */
+  int n_range_compute;       /* clocks around center_mhz (FMA model)        */
+  int n_range_memory;        /* clocks around center_mem_mhz                */
 } ct_steer_result;
 
+/* which_bench value of ct_tune_steered: both models, union of their ranges */
+enum { CT_STEER_UNION = 3 };
+
 /*
- * Model-steered tuning (Section IV-E): sweep the microbenchmark `which_bench`
- * over fit_clocks (>= 3), fit the power model (f = the locked clocks), take
- * the supported clocks (NULL: the platform's list) within +-rel_halfwidth of
- * the predicted optimum and run ct_tune over that range only.  records /
- * n_records / best_index as ct_tune; range_out (optional) receives the
- * range.
+ * Model-steered tuning (Section IV-E): sweep a microbenchmark over
+ * fit_clocks (>= 3), fit, take the supported clocks (NULL: the platform's
+ * list) within +-rel_halfwidth of the predicted optimum and run ct_tune over
+ * that range only.  which_bench:
+ *   CT_UNIT_FMA     the paper's model: Eq. powercurve on the FMA-dense
+ *                   sweep, optimum of P*(f)/f (compute-bound kernels);
+ *   CT_UNIT_COPY    the memory-aware model on the stream-copy sweep: power
+ *                   and time fits, optimum of P*(f) t(f) (memory-bound
+ *                   kernels); `model` / `center_mhz` repeat the copy fit;
+ *   CT_STEER_UNION  both sweeps; the union of the two ranges (a kernel whose
+ *                   boundness is unknown).
+ * The fits use the requested clocks as f.  records / n_records / best_index
+ * as ct_tune; range_out (optional) receives the tuned range.
  */
 int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
                     const int* fit_clocks, int n_fit_clocks, const int* supported,
@@ -530,23 +603,37 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
  *
  * It runs the same persistent batched kernel as ct_batch_run on the same
  * caller-owned inputs and outputs, but every piece of scratch it needs (work
- * counter, status word, image table, padded taps) lives in one fixed array
+ * counters, status word, image table, padded taps) lives in one fixed array
  * compiled into the library (about 373 KB, held on every GPU that loads the
  * library until the process exits).  Limit: n <= 256 images (filter sides
  * 1..17, odd); larger n returns CT_EINVAL and ct_last_error() says why.  No
- * cudaMalloc, cudaFree or other allocating routine is called.  The taps are
- * copied from `filt` (host) on `stream`; the call returns without
- * synchronising (inputs must stay alive until the work completes).
+ * cudaMalloc, cudaFree or other allocating routine is called.  The image
+ * table and the taps (read from `filt`, host) go to the device as one copy
+ * on `stream` from a per-thread host block in pageable memory; the runtime
+ * stages such a copy before it returns and may first wait for work already
+ * queued on `stream`, so the call can block until that work is done.  It
+ * does not wait for its own kernels (inputs and outputs must stay alive
+ * until the work completes).
  *
  * The first call on a device resolves the array's device address and raises
  * the kernel's shared-memory limit; make that first call before any stream
  * capture.  Every call reuses the same array (its contents are those of the
- * last call; the work counter is cleared each call), so calls whose work
+ * last call; the work counters are cleared each call), so calls whose work
  * overlaps on the GPU -- different streams, or different host threads --
  * race: serialise them on one stream.
  */
 int ct_batch_run_noalloc(const ct_batch_item* items, int n, const ct_batch_tiles* tiles_or_null,
                          void* stream);
+/*
+ * The status word of the no-allocation scratch, also without allocating:
+ * error bits the batched kernels raised in ct_batch_run_noalloc calls
+ * (bit 2, as in ct_status_read: a work item outside its image, or a filter
+ * side the launch's kernel does not hold).  The word is zero when the library loads
+ * and keeps its bits across calls until this function clears it (clear != 0).
+ * Reads on `stream` and waits for it, so the bits cover every call enqueued
+ * there before; *bits receives the word.
+ */
+int ct_batch_noalloc_status(unsigned* bits, int clear, void* stream);
 
 
 /* ---- request server with continuous batching ---------------------------- */

@@ -44,6 +44,7 @@ class CtDeviceInfo(ctypes.Structure):
 
 
 CT_UNIT_CONV, CT_UNIT_FMA, CT_UNIT_COPY = 0, 1, 2
+CT_STEER_UNION = 3
 CT_OBJ_TIME, CT_OBJ_ENERGY, CT_OBJ_GFLOPS_PER_W = 0, 1, 2
 CT_SPACE_BASIC, CT_SPACE_FULL = 0, 1
 REC_THROTTLED, REC_COTENANT, REC_DEFAULT_CLOCKS, REC_INVALID, REC_CACHED, REC_NO_ENERGY, \
@@ -111,9 +112,27 @@ class CtTuneOptions(ctypes.Structure):
                 ("settle_s", c_double), ("fallback_default_clocks", c_int)]
 
 
+class CtTimeModel(ctypes.Structure):
+    _fields_ = [("t_mem_s", c_double), ("c_core_s_ghz", c_double), ("sse", c_double),
+                ("n_used", c_int), ("f_lo_mhz", c_double), ("f_thr_mhz", c_double)]
+
+    def to_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "CtTimeModel":
+        m = cls()
+        for k, _ in cls._fields_:
+            setattr(m, k, d[k])
+        return m
+
+
 class CtSteerResult(ctypes.Structure):
     _fields_ = [("model", CtPowerModel), ("center_mhz", c_double), ("n_range", c_int),
-                ("fit_wall_s", c_double), ("tune_wall_s", c_double)]
+                ("fit_wall_s", c_double), ("tune_wall_s", c_double),
+                ("model_mem", CtPowerModel), ("time_mem", CtTimeModel),
+                ("center_mem_mhz", c_double), ("n_range_compute", c_int),
+                ("n_range_memory", c_int)]
 
 
 class ConvTuneError(RuntimeError):
@@ -176,6 +195,10 @@ _SIGS = {
                                    c_void_p]),
     "ct_model_power": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "ct_optimal_clock": (c_int, [c_void_p, c_void_p]),
+    "ct_fit_time_model": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "ct_model_time": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    "ct_memory_aware_optimum": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ct_clock_range": (c_int, [c_double, c_void_p, c_int, c_double, c_void_p, c_int, c_void_p]),
     "ct_pick_clock_range": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_int,
                                     c_void_p, c_void_p]),
     "ct_space": (c_int, [c_int, c_void_p, c_int, c_void_p]),
@@ -196,6 +219,7 @@ _SIGS = {
     "ct_batch_tune": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_int, c_void_p]),
     "ct_batch_run_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "ct_batch_noalloc_status": (c_int, [c_void_p, c_int, c_void_p]),
     "ct_server_create": (c_int, [c_void_p, c_void_p]),
     "ct_server_submit": (c_int, [c_void_p, c_void_p, c_long, c_void_p, c_int, c_void_p, c_long,
                                  c_int, c_int, c_void_p]),
@@ -461,6 +485,48 @@ def pick_clock_range(model: dict, supported_mhz, rel_halfwidth=0.10, center="opt
     return [int(x) for x in out[:n.value]], c0.value
 
 
+# ---- memory-aware energy model ----------------------------------------------
+def fit_time_model(f_mhz, t_s, throttled=None) -> dict:
+    """t(f) = t_mem + c_core / f by non-negative least squares (ct_fit_time_model)."""
+    f, fp = _darr(f_mhz)
+    t, tp = _darr(t_s)
+    if f.shape != t.shape:
+        raise ValueError("f and t differ in length")
+    th = np.ascontiguousarray(throttled, dtype=np.int32) if throttled is not None else None
+    m = CtTimeModel()
+    _check(lib().ct_fit_time_model(fp, tp, th.ctypes.data if th is not None else None, f.size,
+                                   ctypes.byref(m)), "ct_fit_time_model")
+    return m.to_dict()
+
+
+def model_time(tm: dict, f_mhz):
+    f, fp = _darr(f_mhz)
+    out = np.empty_like(f)
+    m = CtTimeModel.from_dict(tm)
+    _check(lib().ct_model_time(ctypes.byref(m), fp, f.size, out.ctypes.data), "ct_model_time")
+    return out
+
+
+def memory_aware_optimum(pm: dict, tm: dict):
+    """(f_opt_mhz, E there) of P*(f) t(f) (ct_memory_aware_optimum)."""
+    p = CtPowerModel.from_dict(pm)
+    t = CtTimeModel.from_dict(tm)
+    f, e = c_double(0), c_double(0)
+    _check(lib().ct_memory_aware_optimum(ctypes.byref(p), ctypes.byref(t), ctypes.byref(f),
+                                         ctypes.byref(e)), "ct_memory_aware_optimum")
+    return f.value, e.value
+
+
+def clock_range(center_mhz, supported_mhz, rel_halfwidth=0.10):
+    sup = np.ascontiguousarray(supported_mhz, dtype=np.int32)
+    out = np.zeros(max(1, sup.size), dtype=np.int32)
+    n = c_int(0)
+    _check(lib().ct_clock_range(float(center_mhz), sup.ctypes.data, sup.size,
+                                float(rel_halfwidth), out.ctypes.data, out.size, ctypes.byref(n)),
+           "ct_clock_range")
+    return [int(x) for x in out[:n.value]]
+
+
 # ---- tuning -----------------------------------------------------------------
 def space(which=CT_SPACE_BASIC) -> list:
     n = c_int(0)
@@ -573,7 +639,10 @@ def tune_steered(inp, filt, out, out_h, out_w, fit_clocks, cfgs=None, supported=
                                  rng.ctypes.data, rng.size, recs, cap, ctypes.byref(n),
                                  ctypes.byref(best)), "ct_tune_steered")
     result = dict(model=res.model.to_dict(), center_mhz=res.center_mhz, n_range=res.n_range,
-                  fit_wall_s=res.fit_wall_s, tune_wall_s=res.tune_wall_s)
+                  fit_wall_s=res.fit_wall_s, tune_wall_s=res.tune_wall_s,
+                  model_mem=res.model_mem.to_dict(), time_mem=res.time_mem.to_dict(),
+                  center_mem_mhz=res.center_mem_mhz, n_range_compute=res.n_range_compute,
+                  n_range_memory=res.n_range_memory)
     return result, [int(x) for x in rng[:res.n_range]], \
         [recs[i].to_dict() for i in range(n.value)], best.value
 

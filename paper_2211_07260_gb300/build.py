@@ -61,8 +61,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     newest = _newest_dep()
+    # host code: no contraction of a*b+c into FMA (aarch64 hosts would
+    # otherwise round the FP64 model arithmetic differently from x86-64)
     common = ["-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-              "-I", INCLUDE, "-I", CSRC]
+              "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
     def compile_one(unit):
         obj, src, extra = unit

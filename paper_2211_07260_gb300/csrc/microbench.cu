@@ -200,22 +200,12 @@ int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
                     int* best_index) {
   if (!p || !opt || !res || !n_records || !best_index || !fit_clocks || n_fit_clocks < 3)
     return CT_EINVAL;
-  if (which_bench != CT_UNIT_FMA && which_bench != CT_UNIT_COPY) return CT_EINVAL;
+  if (which_bench != CT_UNIT_FMA && which_bench != CT_UNIT_COPY && which_bench != CT_STEER_UNION)
+    return CT_EINVAL;
   memset(res, 0, sizeof(*res));
   const ct_platform_ops ops = platform_ops();
   const ct_measure_options mo = resolve_options(&opt->measure);
   const double t0 = platform_now(ops);
-  std::vector<double> f(n_fit_clocks), pw(n_fit_clocks);
-  std::vector<int> thr(n_fit_clocks);
-  int rc = power_samples(which_bench, fit_clocks, n_fit_clocks, mo, ops, (cudaStream_t)stream,
-                         f.data(), pw.data(), thr.data(), nullptr);
-  if (rc != CT_OK) return rc;
-  // the fit uses the requested (locked) clocks as f; the measured clock
-  // decides only whether a sample throttled
-  std::vector<double> freq(fit_clocks, fit_clocks + n_fit_clocks);
-  rc = ct_fit_power_model(freq.data(), pw.data(), nullptr, thr.data(), n_fit_clocks, 0.0,
-                          &res->model);
-  if (rc != CT_OK) return rc;
   std::vector<int> sup;
   if (supported && n_supported > 0) {
     sup.assign(supported, supported + n_supported);
@@ -223,16 +213,64 @@ int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
     if (!ops.supported_sm_clocks) return CT_ENOTSUP;
     sup.resize(1024);
     int ns = 0;
-    rc = ops.supported_sm_clocks(ops.ctx, sup.data(), (int)sup.size(), &ns);
+    const int rc = ops.supported_sm_clocks(ops.ctx, sup.data(), (int)sup.size(), &ns);
     if (rc != CT_OK) return rc;
     sup.resize(ns);
   }
-  std::vector<int> range(sup.size());
-  int nr = 0;
-  rc = ct_pick_clock_range(&res->model, sup.data(), (int)sup.size(), rel_halfwidth, 0,
-                           range.data(), (int)range.size(), &nr, &res->center_mhz);
-  if (rc != CT_OK) return rc;
-  range.resize(nr);
+  // the fits use the requested (locked) clocks as f; the measured clock
+  // decides only whether a sample throttled
+  const std::vector<double> freq(fit_clocks, fit_clocks + n_fit_clocks);
+  std::vector<double> f(n_fit_clocks), pw(n_fit_clocks), ts(n_fit_clocks);
+  std::vector<int> thr(n_fit_clocks);
+  std::vector<ct_record> recs(n_fit_clocks);
+  std::vector<int> range_c, range_m;
+  int rc = CT_OK;
+  if (which_bench == CT_UNIT_FMA || which_bench == CT_STEER_UNION) {
+    // compute-bound model (Section IV-E): P*(f)/f on the FMA-dense sweep
+    rc = power_samples(CT_UNIT_FMA, fit_clocks, n_fit_clocks, mo, ops, (cudaStream_t)stream,
+                       f.data(), pw.data(), thr.data(), nullptr);
+    if (rc != CT_OK) return rc;
+    rc = ct_fit_power_model(freq.data(), pw.data(), nullptr, thr.data(), n_fit_clocks, 0.0,
+                            &res->model);
+    if (rc != CT_OK) return rc;
+    range_c.resize(sup.size());
+    int nr = 0;
+    rc = ct_pick_clock_range(&res->model, sup.data(), (int)sup.size(), rel_halfwidth, 0,
+                             range_c.data(), (int)range_c.size(), &nr, &res->center_mhz);
+    if (rc != CT_OK) return rc;
+    range_c.resize(nr);
+  }
+  if (which_bench == CT_UNIT_COPY || which_bench == CT_STEER_UNION) {
+    // memory-aware model: P*(f) t(f) on the stream-copy sweep
+    rc = power_samples(CT_UNIT_COPY, fit_clocks, n_fit_clocks, mo, ops, (cudaStream_t)stream,
+                       f.data(), pw.data(), thr.data(), recs.data());
+    if (rc != CT_OK) return rc;
+    for (int i = 0; i < n_fit_clocks; ++i) ts[i] = recs[i].t_s;
+    rc = ct_fit_power_model(freq.data(), pw.data(), nullptr, thr.data(), n_fit_clocks, 0.0,
+                            &res->model_mem);
+    if (rc != CT_OK) return rc;
+    rc = ct_fit_time_model(freq.data(), ts.data(), thr.data(), n_fit_clocks, &res->time_mem);
+    if (rc != CT_OK) return rc;
+    rc = ct_memory_aware_optimum(&res->model_mem, &res->time_mem, &res->center_mem_mhz, nullptr);
+    if (rc != CT_OK) return rc;
+    range_m.resize(sup.size());
+    int nr = 0;
+    rc = ct_clock_range(res->center_mem_mhz, sup.data(), (int)sup.size(), rel_halfwidth,
+                        range_m.data(), (int)range_m.size(), &nr);
+    if (rc != CT_OK) return rc;
+    range_m.resize(nr);
+    if (which_bench == CT_UNIT_COPY) {
+      res->model = res->model_mem;
+      res->center_mhz = res->center_mem_mhz;
+    }
+  }
+  res->n_range_compute = (int)range_c.size();
+  res->n_range_memory = (int)range_m.size();
+  std::vector<int> range = range_c;
+  range.insert(range.end(), range_m.begin(), range_m.end());
+  std::sort(range.begin(), range.end());
+  range.erase(std::unique(range.begin(), range.end()), range.end());
+  const int nr = (int)range.size();
   res->n_range = nr;
   if (range_out) {
     if (nr > range_cap) return CT_ENOMEM;

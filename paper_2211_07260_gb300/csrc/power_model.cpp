@@ -405,3 +405,149 @@ int ct_pick_clock_range(const ct_power_model* m, const int* supported_mhz, int n
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Memory-aware energy model (Sections II and IV-F): t(f) = t_mem + c_core / f
+// by non-negative least squares in (1, 1/f), E(f) = P*(f) t(f), minimised over
+// the integer-MHz clocks both fits cover.
+// ---------------------------------------------------------------------------
+namespace {
+
+double time_sse(const std::vector<double>& u, const std::vector<double>& t, double a, double b) {
+  double acc = 0;
+  for (size_t i = 0; i < u.size(); ++i) {
+    const double r = t[i] - (a + b * u[i]);
+    acc += r * r;
+  }
+  return acc;
+}
+
+double model_time_at(const ct_time_model& tm, double f_mhz) {
+  return tm.t_mem_s + tm.c_core_s_ghz / (f_mhz / 1000.0);
+}
+
+double model_energy_at(const ct_power_model& pm, const ct_time_model& tm, double f_mhz) {
+  return std::min(pm.p_max_w, model_q(pm, f_mhz / 1000.0)) * model_time_at(tm, f_mhz);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ct_fit_time_model(const double* f_mhz, const double* t_s, const int* throttled_or_null,
+                      int n, ct_time_model* out) {
+  if (!f_mhz || !t_s || !out || n < 0) return CT_EINVAL;
+  memset(out, 0, sizeof(*out));
+  std::vector<double> u, t, fk;
+  for (int i = 0; i < n; ++i) {
+    if (!isfinite(f_mhz[i]) || f_mhz[i] <= 0 || !isfinite(t_s[i])) return CT_EINVAL;
+    if (throttled_or_null && throttled_or_null[i]) continue;
+    fk.push_back(f_mhz[i]);
+    u.push_back(1000.0 / f_mhz[i]);
+    t.push_back(t_s[i]);
+  }
+  if (fk.size() < 2) return CT_EINVAL;
+  const size_t m = u.size();
+  double um = 0, tmn = 0;
+  for (size_t i = 0; i < m; ++i) {
+    um += u[i];
+    tmn += t[i];
+  }
+  um /= m;
+  tmn /= m;
+  double suu = 0, sut = 0, tu = 0, uu = 0;
+  for (size_t i = 0; i < m; ++i) {
+    suu += (u[i] - um) * (u[i] - um);
+    sut += (u[i] - um) * (t[i] - tmn);
+    tu += t[i] * u[i];
+    uu += u[i] * u[i];
+  }
+  // candidates: the unconstrained solution if feasible, then the faces
+  // t_mem = 0 and c_core = 0 (first least residual wins)
+  double cand[3][2];
+  int nc = 0;
+  if (suu > 0) {
+    const double b = sut / suu, a = tmn - b * um;
+    if (a >= 0 && b >= 0) {
+      cand[nc][0] = a;
+      cand[nc][1] = b;
+      ++nc;
+    }
+  }
+  cand[nc][0] = 0.0;
+  cand[nc][1] = std::max(0.0, tu / uu);
+  ++nc;
+  cand[nc][0] = std::max(0.0, tmn);
+  cand[nc][1] = 0.0;
+  ++nc;
+  int best = 0;
+  double best_s = time_sse(u, t, cand[0][0], cand[0][1]);
+  for (int c = 1; c < nc; ++c) {
+    const double sc = time_sse(u, t, cand[c][0], cand[c][1]);
+    if (sc < best_s) {
+      best_s = sc;
+      best = c;
+    }
+  }
+  out->t_mem_s = cand[best][0];
+  out->c_core_s_ghz = cand[best][1];
+  out->sse = best_s;
+  out->n_used = (int)m;
+  out->f_lo_mhz = *std::min_element(fk.begin(), fk.end());
+  out->f_thr_mhz = *std::max_element(fk.begin(), fk.end());
+  return CT_OK;
+}
+
+int ct_model_time(const ct_time_model* tm, const double* f_mhz, int n, double* t_s) {
+  if (!tm || !f_mhz || !t_s || n < 0) return CT_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!(f_mhz[i] > 0)) return CT_EINVAL;
+    t_s[i] = model_time_at(*tm, f_mhz[i]);
+  }
+  return CT_OK;
+}
+
+int ct_memory_aware_optimum(const ct_power_model* pm, const ct_time_model* tm,
+                            double* f_opt_mhz, double* e_opt_j) {
+  if (!pm || !tm || !f_opt_mhz || pm->has_voltage) return CT_EINVAL;
+  const double lo = std::max(pm->f_lo_mhz, tm->f_lo_mhz);
+  const double hi = std::min(pm->f_thr_mhz, tm->f_thr_mhz);
+  const long glo = (long)ceil(lo), ghi = (long)floor(hi);
+  if (!(glo > 0) || ghi < glo) return CT_EINVAL;
+  double best_f = (double)glo, best_e = model_energy_at(*pm, *tm, (double)glo);
+  for (long f = glo + 1; f <= ghi; ++f) {
+    const double e = model_energy_at(*pm, *tm, (double)f);
+    if (e < best_e) {  // strict: ties keep the lower clock
+      best_e = e;
+      best_f = (double)f;
+    }
+  }
+  *f_opt_mhz = best_f;
+  if (e_opt_j) *e_opt_j = best_e;
+  return CT_OK;
+}
+
+int ct_clock_range(double center_mhz, const int* supported_mhz, int n_supported,
+                   double rel_halfwidth, int* out_mhz, int cap, int* n_out) {
+  if (!supported_mhz || n_supported <= 0 || !n_out || rel_halfwidth < 0 ||
+      !isfinite(center_mhz))
+    return CT_EINVAL;
+  std::vector<int> sup(supported_mhz, supported_mhz + n_supported);
+  std::sort(sup.begin(), sup.end());
+  const double lo = (1.0 - rel_halfwidth) * center_mhz, hi = (1.0 + rel_halfwidth) * center_mhz;
+  std::vector<int> sel;
+  for (int c : sup)
+    if (c >= lo && c <= hi) sel.push_back(c);
+  if (sel.empty()) {
+    int best = sup[0];
+    for (int c : sup)
+      if (fabs(c - center_mhz) < fabs(best - center_mhz)) best = c;
+    sel.push_back(best);
+  }
+  *n_out = (int)sel.size();
+  if ((int)sel.size() > cap || (!out_mhz && cap > 0)) return CT_ENOMEM;
+  for (size_t i = 0; i < sel.size(); ++i) out_mhz[i] = sel[i];
+  return CT_OK;
+}
+
+}  // extern "C"
