@@ -3,6 +3,7 @@
 // tuning with the energy objective, and the plain one-launch-per-image
 // comparison.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -666,14 +667,48 @@ struct NoAllocDevice {
 
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[64];
-// host copy of the image table, per thread
-thread_local BatchImage t_noalloc_table[kNoAllocMaxImages];
+// host mirror of the scratch's table and tap regions, per thread: one copy
+// sends the image table and the padded taps of a call
+struct NoAllocHostBlock {
+  BatchImage table[kNoAllocMaxImages];
+  float taps[(size_t)kNoAllocTapFloats * kNoAllocMaxImages];
+};
+static_assert(sizeof(BatchImage) * kNoAllocMaxImages == kNoAllocTableBytes, "table region");
+thread_local NoAllocHostBlock t_noalloc_host;
 
 }  // namespace
 
 // The scratch itself.  In host code this name is only a stand-in for the
 // device array: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+// Once per device, with that device current: resolve the array's device
+// address.
+int noalloc_device(NoAllocDevice* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= 64) return CT_ENOTSUP;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return cuda_status(e);
+    d.base = static_cast<unsigned char*>(p);
+    d.ready = true;
+  }
+  *out = d;
+  return CT_OK;
+}
+
+// The status word sits in the last word of the counter header.
+unsigned* noalloc_status_word(const NoAllocDevice& nd) {
+  return reinterpret_cast<unsigned*>(nd.base) + kBatchMaxLaunches;
+}
+
+}  // namespace
 
 extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
                                     const ct_batch_tiles* tiles, void* stream) {
@@ -682,24 +717,9 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
     set_last_error("ct_batch_run_noalloc: more images than the fixed scratch holds (limit 256)");
     return CT_EINVAL;
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_status(e);
-  if (dev < 0 || dev >= 64) return CT_ENOTSUP;
   NoAllocDevice nd;
-  {
-    // once per device, with that device current: resolve the array's device
-    // address (the class kernels' shared-memory caps are raised by the plan)
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    NoAllocDevice& d = g_noalloc_dev[dev];
-    if (!d.ready) {
-      void* p = nullptr;
-      if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return cuda_status(e);
-      d.base = static_cast<unsigned char*>(p);
-      d.ready = true;
-    }
-    nd = d;
-  }
+  int rc = noalloc_device(&nd);
+  if (rc != CT_OK) return rc;
 
   // validate, and order the images by (filter side, size class)
   int idx[kNoAllocMaxImages];
@@ -726,15 +746,17 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   if (m == 0) return CT_OK;
 
   cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
   // header: one work counter per launch, the status word in its last word
   unsigned* counters = reinterpret_cast<unsigned*>(nd.base);
-  unsigned* status = counters + kBatchMaxLaunches;
+  unsigned* status = noalloc_status_word(nd);
   BatchImage* d_table = reinterpret_cast<BatchImage*>(nd.base + kNoAllocHeaderBytes);
   float* d_taps = reinterpret_cast<float*>(nd.base + kNoAllocHeaderBytes + kNoAllocTableBytes);
+  NoAllocHostBlock& hb = t_noalloc_host;
   long long first = 0;
   for (int q = 0; q < m; ++q) {
     const ct_batch_item& it = items[idx[q]];
-    BatchImage& im = t_noalloc_table[q];
+    BatchImage& im = hb.table[q];
     memset(&im, 0, sizeof(im));
     im.tap_off = -1;
     im.in = it.in;
@@ -762,28 +784,42 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
     im.first_item = first;
     first += (long long)im.tiles_x * im.tiles_y;
     // taps: k rows padded to round_up(k, 4) floats (the padding is never used
-    // as a tap), copied straight from the caller's host array
+    // as a tap) in this image's slot of the tap region
     const int kp = round_up(it.k, 4);
-    float* dst = d_taps + (size_t)q * kNoAllocTapFloats;
-    im.filt = dst;
-    e = cudaMemcpy2DAsync(dst, sizeof(float) * kp, it.filt, sizeof(float) * it.k,
-                          sizeof(float) * it.k, it.k, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
+    float* slot = hb.taps + (size_t)q * kNoAllocTapFloats;
+    for (int j = 0; j < it.k; ++j)
+      for (int i = 0; i < kp; ++i) slot[j * kp + i] = i < it.k ? it.filt[j * it.k + i] : 0.0f;
+    im.filt = d_taps + (size_t)q * kNoAllocTapFloats;
   }
-  // the plan places the 13..17 taps in parameter blocks (it sets tap_off,
+  // the plan places taps in parameter blocks where they fit (it sets tap_off,
   // so the table goes to the device after it)
   const float* host_taps[kNoAllocMaxImages];
   for (int q = 0; q < m; ++q) host_taps[q] = items[idx[q]].filt;
   BatchPlan plan;
-  const int rc = plan_batch(t_noalloc_table, m, host_taps, &plan);
+  rc = plan_batch(hb.table, m, host_taps, &plan);
   if (rc != CT_OK) return rc;
-  if ((e = cudaMemcpyAsync(d_table, t_noalloc_table, sizeof(BatchImage) * m,
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  // one copy: the whole table region, then the m tap slots right behind it
+  // (the two regions are adjacent in the scratch and in the host mirror)
+  static_assert(offsetof(NoAllocHostBlock, taps) == kNoAllocTableBytes, "host mirror layout");
+  const size_t bytes = kNoAllocTableBytes + sizeof(float) * (size_t)kNoAllocTapFloats * m;
+  if ((e = cudaMemcpyAsync(d_table, &hb, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_status(e);
-  // the status word starts clear (the counters are zeroed with the launches)
-  if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), s)) != cudaSuccess)
-    return cuda_status(e);
+  // the counters are zeroed with the launches; the status word (zero when
+  // the library loads) keeps its bits until ct_batch_noalloc_status clears it
   return enqueue_batch_plan(plan, d_table, counters, status, s);
+}
+
+extern "C" int ct_batch_noalloc_status(unsigned* bits, int clear, void* stream) {
+  if (!bits) return CT_EINVAL;
+  NoAllocDevice nd;
+  int rc = noalloc_device(&nd);
+  if (rc != CT_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* status = noalloc_status_word(nd);
+  cudaError_t e = cudaMemcpyAsync(bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && clear) e = cudaMemsetAsync(status, 0, sizeof(unsigned), s);
+  return cuda_status(e);
 }
 
 // ---------------------------------------------------------------------------

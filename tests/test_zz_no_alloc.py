@@ -37,6 +37,14 @@ def _run_noalloc(ents, stream):
     return rc, keep
 
 
+def _noalloc_status(stream, clear=True):
+    bits = ctypes.c_uint(0xFFFFFFFF)
+    rc = api.lib().ct_batch_noalloc_status(ctypes.byref(bits), int(clear),
+                                           ctypes.c_void_p(stream.cuda_stream))
+    assert rc == api.CT_OK, api.lib().ct_last_error()
+    return bits.value
+
+
 @pytest.mark.parametrize("seed", [11])
 def test_noalloc_matches_the_allocating_entry_point_on_two_calls(seed):
     stream = torch.cuda.Stream()
@@ -44,16 +52,31 @@ def test_noalloc_matches_the_allocating_entry_point_on_two_calls(seed):
     batches = [synth.batch_problems(48, seed, lo=17, hi=400),
                synth.batch_problems(30, seed + 1, lo=100, hi=700)
                + [synth.conv_problem(33, 45, 9, seed=[seed, 7], pitch_align=1)]]
+    staged = [(probs,) + _device(probs) for probs in batches]
+    torch.cuda.synchronize()
     results = []
     keeps = []
-    for probs in batches:
-        ents, outs = _device(probs)
-        torch.cuda.synchronize()
+    for probs, ents, outs in staged:
         rc, keep = _run_noalloc(ents, stream)
         keeps.append(keep)
         assert rc == api.CT_OK, api.lib().ct_last_error()
+        # the kernels raised no error bit in this call
+        assert _noalloc_status(stream) == 0
         results.append((probs, outs))
     stream.synchronize()
+    # once set up (and its kernels loaded), further calls take no device
+    # memory: neither from torch's caching allocator nor from the device
+    reserved = torch.cuda.memory_reserved()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        for probs, ents, outs in staged:
+            rc, keep = _run_noalloc(ents, stream)
+            keeps.append(keep)
+            assert rc == api.CT_OK, api.lib().ct_last_error()
+    assert _noalloc_status(stream) == 0
+    stream.synchronize()
+    assert torch.cuda.memory_reserved() == reserved
+    assert torch.cuda.mem_get_info()[0] == free0
     for probs, outs in results:
         ents_ref, outs_ref = _device(probs)
         with api.Batch(ents_ref) as b:
@@ -78,4 +101,5 @@ def test_noalloc_rejects_more_images_than_the_scratch_holds():
     rc, _ = _run_noalloc(ents * 256, stream)  # the limit itself is accepted
     stream.synchronize()
     assert rc == api.CT_OK
+    assert _noalloc_status(stream) == 0
     assert max_rel_err(outs[0].cpu().numpy()[:, :8], oracle_ref(p)) <= MAX_REL
