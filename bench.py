@@ -10,6 +10,21 @@ resident in HBM and L2 is flushed (a 256 MiB write) between timed launches.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl convtune|reference]
 
+At N = 1 the same line also carries, each with its own SM-clock record:
+  roofline.peak_empirical_fma_kernel  the FMA-dense microbenchmark's TFLOP/s
+                                      beside the derived FP32 peak;
+  config1_1024x1024_k7                1024 x 1024 / 7 x 7 at its energy-tuned
+                                      configuration, graph-replayed and with
+                                      L2 flushed, against min(FP32, AI x HBM);
+  batched256                          the 256-image batch as one CUDA-graph
+                                      launch of the persistent kernels vs one
+                                      plain launch per image (GFLOP/s, GFLOP/J,
+                                      mixed roofline, FP64 oracle baseline);
+  serving                             Poisson requests through the continuous-
+                                      batching server vs one plain kernel per
+                                      request (p50 / p99, J per request).
+(--no-extras leaves them out.)
+
 Under torchrun (N > 1) every rank runs its own replica (no exchange step:
 weak scaling); rank 0 prints whole-job throughput.  --impl reference times
 the CPU oracle (FP64 direct correlation, OpenMP) on bands of the same
@@ -53,6 +68,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-energy", action="store_true", help="skip the energy window")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only (no 1024^2 / batched / serving / FMA-peak keys)")
+    ap.add_argument("--serve-rate", type=float, default=5000.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-payloads", type=int, default=64)
     return ap.parse_args()
 
 
@@ -221,63 +241,266 @@ def run_reference(args, world, rank):
     }))
 
 
-def run_batched(args, world, rank, local):
-    """The batched workload: GFLOP/s and GFLOP/J of the persistent launch and of
-    one plain launch per image, both measured by the library's energy window."""
+def load_tiles(api):
+    """Per-bucket batched tiles of this device from tuned_configs.json."""
+    path = os.path.join(ROOT, "paper_2211_07260_gb300", "tuned_configs.json")
+    if os.path.exists(path):
+        t = json.load(open(path)).get("batched_tiles", {}).get(api.device_info()["name"])
+        if t:
+            return ({tuple(int(x) for x in k.split(",")): tuple(v) for k, v in t.items()},
+                    "tuned_configs.json (energy objective per bucket)")
+    return None, "default tiles"
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU pool (GB/s), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "MEASURED_PEAKS.json (measured copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def fp32_peak(sm, mhz):
+    """FP32 FMA peak (FLOP/s) from the unit counts and an SM clock."""
+    return sm * FP32_LANES_PER_SM * 2 * mhz * 1e6
+
+
+def clocks_summary(c):
+    if not c:
+        return None
+    return {"sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"], "reasons": c["reasons"],
+            "power_w_median": c["power_w_median"], "samples_under_load": c["samples_under_load"]}
+
+
+def timed_steps(world, stream, steps, launch, flush=None):
+    """Per-step CUDA-event times (s) of `launch` on `stream`, with an optional
+    L2 flush before each step outside the timed span."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s, e in ev:
+            if flush is not None:
+                flush.zero_()
+            s.record(stream)
+            launch()
+            e.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return [s.elapsed_time(e) / 1e3 for s, e in ev]
+
+
+def batched_oracle_baseline(probs, seconds):
+    """The FP64 oracle on the batch's images in order, until `seconds` pass."""
+    import oracle
+    from oracle import selection
+    nt = oracle.max_threads()
+    t0 = time.perf_counter()
+    flop, done = 0.0, 0
+    for p in probs:
+        oracle.conv2d(p.inp, p.filt, in_w=p.in_w, nthreads=nt)
+        flop += selection.conv2d_flop(p.fh, p.fw, p.out_h, p.out_w)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=flop / dt / 1e9, unit="GFLOP/s", cores=nt, kind="oracle",
+                sample=f"{done} of {len(probs)} batch images in order (FP64 direct correlation, "
+                       f"{flop / 1e9:.1f} GFLOP), {dt:.1f} s wall, {nt} OpenMP threads")
+
+
+def measure_batched(args, world, local, steps, warmup, cpu_seconds):
+    """The 256-image batch: one CUDA-graph launch of the persistent class
+    kernels against one plain launch per image, timed by CUDA events and by
+    the library's energy window, with an SM-clock record."""
     import torch
 
     from paper_2211_07260_gb300 import api, synth
-    torch.cuda.set_device(local)
-    wl = WORKLOADS[args.workload]
+    wl = WORKLOADS["batched256"]
     probs = synth.batch_problems(wl["n"], wl["seed"])
     ents = []
     for p in probs:
         d_in = torch.from_numpy(p.inp).cuda()
         out = torch.empty((p.out_h, (p.out_w + 3) // 4 * 4), dtype=torch.float32, device="cuda")
         ents.append((d_in, p.filt, out, p.out_h, p.out_w))
-    tiles, src = None, "default tiles"
-    path = os.path.join(ROOT, "paper_2211_07260_gb300", "tuned_configs.json")
-    if os.path.exists(path):
-        t = json.load(open(path)).get("batched_tiles", {}).get(api.device_info()["name"])
-        if t:
-            tiles = {tuple(int(x) for x in k.split(",")): tuple(v) for k, v in t.items()}
-            src = "tuned_configs.json (energy objective per bucket)"
+    tiles, src = load_tiles(api)
     opts = api.measure_options(window_s=args.energy_window)
+    info = api.device_info()
+    b_hbm, b_src = hbm_peak_gbs()
+    stream = torch.cuda.Stream()
+    sampler = ClockSampler(local)
     with api.Batch(ents, tiles) as b:
         st = b.info()
-        stream = torch.cuda.Stream()
-        for _ in range(max(3, args.warmup)):
+        for _ in range(max(3, warmup)):
             b.run(stream)
-        barrier(world)
+        b.run_plain(stream)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            b.run(stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        t_s = all_max(world, e0.elapsed_time(e1) / 1e3)
+        sampler.start()
+        t_graph = all_max(world, sum(timed_steps(world, stream, steps, lambda: b.run(stream))))
+        t_plain = all_max(world, sum(timed_steps(world, stream, steps,
+                                                 lambda: b.run_plain(stream))))
         rb = b.measure(False, opts)
         rp = b.measure(True, opts)
+        clocks = sampler.stop()
+    # mixed roofline: per image the slower of its FLOP at the FP32 peak and
+    # its bytes at the HBM copy rate
+    clk = clocks["sm_max_mhz"] if clocks else 2070.0
+    fpk = fp32_peak(info["sm_count"], clk)
+    t_roof = 0.0
+    for p in probs:
+        fl = 2.0 * p.fh * p.fw * p.out_h * p.out_w
+        by = 4.0 * (p.in_h * p.in_w + p.out_h * p.out_w + p.fh * p.fw)
+        t_roof += max(fl / fpk, by / (b_hbm * 1e9))
+    g_graph = st["flop"] * steps / t_graph
+    out = {
+        "workload": "256 images, sides log-uniform [256, 2048], odd k 3..17, seed 2",
+        "images": st["n_images"], "work_items": st["n_items"], "class_launches": st["launches"],
+        "persistent_ctas": st["grid"], "tiles_source": src, "gflop": st["flop"] / 1e9,
+        "l2": "inputs 0.78 GB > L2 (no flush needed)",
+        "graph": {"gflops": g_graph / 1e9, "ms_per_batch": t_graph * 1e3 / steps,
+                  "gflops_energy_window": rb["gflops"], "gflop_per_j": rb["gflops_per_j"],
+                  "power_w_mean": rb["power_w_mean"], "flags": rb["flags"],
+                  "gpu_launches_per_batch": st["launches"]},
+        "plain_per_image": {"gflops": st["flop"] * steps / t_plain / 1e9,
+                            "ms_per_batch": t_plain * 1e3 / steps,
+                            "gflops_energy_window": rp["gflops"],
+                            "gflop_per_j": rp["gflops_per_j"],
+                            "power_w_mean": rp["power_w_mean"], "flags": rp["flags"],
+                            "idle_gaps": bool(rp["flags"] & api.REC_IDLE_GAPS),
+                            "gpu_launches_per_batch": st["n_images"]},
+        "roofline": {"bound": "alu (per image max of FP32 and HBM time)",
+                     "achieved": g_graph / 1e12, "peak": st["flop"] / t_roof / 1e12,
+                     "unit": "TFLOP/s", "frac": t_roof / (t_graph / steps),
+                     "peak_basis": f"sum over images of max(FLOP / {fpk / 1e12:.1f} TFLOP/s, "
+                                   f"bytes / {b_hbm:.0f} GB/s [{b_src}])"},
+        "clocks": clocks_summary(clocks),
+        "note": "idle_gaps: the plain leg's energy window saw the device idle between "
+                "host-issued launches, so its GFLOP/J includes idle power",
+    }
+    if cpu_seconds > 0:
+        out["cpu_baseline"] = batched_oracle_baseline(probs, cpu_seconds)
+    del ents
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_config1(args, world, local, steps, warmup):
+    """1024 x 1024 / 7 x 7 at its energy-tuned configuration: back-to-back
+    graph replay (the tuner's measurement, L2-resident) and single launches
+    with L2 flushed between them."""
+    import torch
+
+    from paper_2211_07260_gb300 import api, synth
+    wl = WORKLOADS["1024x1024_k7"]
+    info = api.device_info()
+    cfg, cfg_src = tuned_config(api, info["name"], wl, None)
+    prob = synth.conv_problem(wl["h"], wl["w"], wl["k"], seed=wl["seed"])
+    flop = 2.0 * wl["k"] ** 2 * wl["h"] * wl["w"]
+    alg_bytes = 4.0 * (prob.in_h * prob.in_w + wl["h"] * wl["w"] + wl["k"] ** 2)
+    stream = torch.cuda.Stream()
+    d_in = torch.from_numpy(prob.inp).cuda()
+    d_out = torch.empty((wl["h"], wl["w"]), dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def launch():
+        api.conv2d_run(d_in, prob.filt, d_out, wl["h"], wl["w"], cfg, stream=stream)
+
+    for _ in range(max(3, warmup)):
+        launch()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_flush = all_max(world, sum(timed_steps(world, stream, steps, launch, flush)))
+    rec = api.measure_conv(d_in, prob.filt, d_out, wl["h"], wl["w"], cfg,
+                           api.measure_options(window_s=args.energy_window), stream=stream)
+    clocks = sampler.stop()
+    b_hbm, b_src = hbm_peak_gbs()
+    clk = clocks["sm_max_mhz"] if clocks else 2070.0
+    fpk = fp32_peak(info["sm_count"], clk)
+    roof = min(fpk, flop / alg_bytes * b_hbm * 1e9)
+    del flush
+    torch.cuda.empty_cache()
+    return {
+        "workload": "1024x1024 output, 7x7 filter, seed 0", "config": list(cfg.as_tuple()),
+        "config_source": cfg_src,
+        "graph_replay": {"gflops": rec["gflops"], "us_per_launch": rec["t_s"] * 1e6,
+                         "gflop_per_j": rec["gflops_per_j"], "power_w_mean": rec["power_w_mean"],
+                         "flags": rec["flags"], "l2": "resident (8.4 MB, back-to-back launches)",
+                         "frac_of_roofline": rec["gflops"] * 1e9 / roof},
+        "l2_flushed": {"gflops": steps * flop / t_flush / 1e9,
+                       "us_per_launch": t_flush * 1e6 / steps,
+                       "frac_of_roofline": steps * flop / t_flush / roof,
+                       "l2": "flushed (256 MiB write) before each timed launch"},
+        "roofline": {"bound": "min(FP32 peak, AI x HBM)", "peak": roof / 1e12, "unit": "TFLOP/s",
+                     "ai_flop_per_byte": flop / alg_bytes,
+                     "peak_basis": f"min({fpk / 1e12:.1f} TFLOP/s, {flop / alg_bytes:.2f} FLOP/B x "
+                                   f"{b_hbm:.0f} GB/s [{b_src}])"},
+        "clocks": clocks_summary(clocks),
+    }
+
+
+def measure_serving(local, rate, seconds, n_payloads):
+    """A short Poisson serving run through the continuous-batching server,
+    then the same arrivals served with one plain kernel per request."""
+    from paper_2211_07260_gb300 import api, serve
+    tiles, src = load_tiles(api)
+    payloads = serve.make_payloads(n_payloads)
+    p_idle = serve.idle_power(0.5)
+    out = {"workload": f"Poisson arrivals at {rate:.0f} req/s for {seconds:.1f} s, shapes of the "
+                       f"batched law (seed 3), {n_payloads} pinned host payloads reused",
+           "tiles_source": src, "p_idle_w": p_idle}
+    for mode in ("batched", "plain"):
+        sampler = ClockSampler(local)
+        sampler.start()
+        r = serve.serve_rate(payloads, rate, seconds, 10 ** 7, plain=(mode == "plain"),
+                             tiles=tiles, p_idle=p_idle)
+        clocks = sampler.stop()
+        out[mode] = {k: r[k] for k in ("requests", "req_per_s", "p50_ms", "p99_ms", "max_ms",
+                                       "j_per_req", "j_per_req_above_idle", "gflop_per_j",
+                                       "mean_batch", "gflops")}
+        out[mode]["clocks"] = clocks_summary(clocks)
+    return out
+
+
+def measure_fp32_peak(local):
+    """The FMA-dense microbenchmark: the empirical FP32 ceiling next to the
+    peak derived from unit counts and the SM clock it ran at."""
+    from paper_2211_07260_gb300 import api
+    info = api.device_info()
+    sampler = ClockSampler(local)
+    sampler.start()
+    r = api.measure_microbench(api.CT_UNIT_FMA, api.measure_options(window_s=0.5))
+    clocks = sampler.stop()
+    clk = r["clock_mhz_meas"] if r["clock_mhz_meas"] > 0 else (clocks or {}).get("sm_mhz", 2070.0)
+    return {"tflops": r["gflops"] / 1e3, "sm_mhz": clk,
+            "derived_peak_tflops_at_that_clock": fp32_peak(info["sm_count"], clk) / 1e12,
+            "frac_of_derived": r["gflops"] * 1e9 / fp32_peak(info["sm_count"], clk),
+            "clocks": clocks_summary(clocks)}
+
+
+def run_batched(args, world, rank, local):
+    """--workload batched256: the batched comparison as the headline line."""
+    import torch
+    torch.cuda.set_device(local)
+    b = measure_batched(args, world, local, args.steps, args.warmup,
+                        0 if (args.no_cpu or world > 1) else args.cpu_seconds)
     if rank != 0:
         return
+    g = b["graph"]
     out = {
-        "metric": METRIC, "value": world * args.steps * st["flop"] / t_s / 1e9, "unit": "GFLOP/s",
+        "metric": METRIC, "value": world * g["gflops"], "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": g["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "images": st["n_images"], "tiles": st["n_items"],
-                   "persistent_ctas": st["grid"], "class_launches": st["launches"],
-                   "tiles_source": src,
-                   "l2": "inputs 1.5 GB > L2", "parallelism": f"replicas x{world}"},
-        "gflop_per_j": rb["gflops_per_j"],
-        "batched": {"gflops": rb["gflops"], "gflop_per_j": rb["gflops_per_j"],
-                    "power_w_mean": rb["power_w_mean"], "flags": rb["flags"]},
-        "plain_per_image": {"gflops": rp["gflops"], "gflop_per_j": rp["gflops_per_j"],
-                            "power_w_mean": rp["power_w_mean"], "flags": rp["flags"]},
-        "gpu_launches": args.steps * st["launches"],
+        "config": {"workload": args.workload, "l2": b["l2"], "parallelism": f"replicas x{world}"},
+        "gflop_per_j": g["gflop_per_j"], "batched": b, "roofline": b["roofline"],
+        "clocks": b["clocks"], "gpu_launches": args.steps * g["gpu_launches_per_batch"],
     }
+    if "cpu_baseline" in b:
+        out["cpu_baseline"] = b["cpu_baseline"]
     print(json.dumps(out))
 
 
@@ -446,6 +669,19 @@ def main():
     }
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if world == 1 and not args.no_extras and args.workload == "4096x4096_k17":
+        # the other workloads at N = 1, each under its own SM-clock record
+        del flush
+        torch.cuda.empty_cache()
+        fp = measure_fp32_peak(local)
+        out["roofline"]["peak_empirical_fma_kernel"] = fp
+        out["config1_1024x1024_k7"] = measure_config1(args, world, local, max(args.steps, 50),
+                                                      args.warmup)
+        out["batched256"] = measure_batched(args, world, local, max(3, min(args.steps, 10)),
+                                            args.warmup, 0 if args.no_cpu else 5.0)
+        if args.serve_seconds > 0:
+            out["serving"] = measure_serving(local, args.serve_rate, args.serve_seconds,
+                                             args.serve_payloads)
     print(json.dumps(out))
 
 
