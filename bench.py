@@ -247,8 +247,7 @@ def load_tiles(api):
     if os.path.exists(path):
         t = json.load(open(path)).get("batched_tiles", {}).get(api.device_info()["name"])
         if t:
-            return ({tuple(int(x) for x in k.split(",")): tuple(v) for k, v in t.items()},
-                    "tuned_configs.json (energy objective per bucket)")
+            return api.tiles_from_json(t), "tuned_configs.json (energy objective per bucket)"
     return None, "default tiles"
 
 

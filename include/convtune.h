@@ -105,8 +105,9 @@ typedef struct {
 /*
  * Check a configuration against a problem and the current device without
  * launching: block shape, register / shared-memory limits, TMA box limits
- * (tile width <= 256 floats), pitch and pointer alignment for the vector
- * width.  Returns CT_OK, CT_EINVAL (problem itself invalid) or CT_ECONFIG
+ * (tile height <= 256 rows; a tile wider than a 256-float box is staged as
+ * one box per group of threads in x, each with its own halo), pitch and
+ * pointer alignment for the vector width.  Returns CT_OK, CT_EINVAL (problem itself invalid) or CT_ECONFIG
  * (configuration pruned).  If `why` is non-NULL and why_cap > 0 a short
  * reason is written there (NUL-terminated).
  */
@@ -205,6 +206,9 @@ int ct_device_info_get(ct_device_info* out);
  * a device setting that outlives the process.  The NVML table refuses it
  * (CT_EPERM) unless the environment variable CONVTUNE_ALLOW_CLOCK_CONTROL
  * is "1"; when enabled, every lock is undone on return, on error and at exit.
+ * Power limits (nvml_pwr_limit) are the same kind of setting: refused unless
+ * CONVTUNE_ALLOW_POWER_CONTROL is "1", and restored to the device's default
+ * on return, on error and at exit.
  */
 enum { CT_UNIT_CONV = 0, CT_UNIT_FMA = 1, CT_UNIT_COPY = 2 };
 /* Throttle-reason bits (same values as NVML's clocks-event reasons). */
@@ -227,6 +231,11 @@ typedef struct {
      `kind` (CT_UNIT_*; cfg is the configuration for CT_UNIT_CONV, else NULL)
      and report their device time in *elapsed_ms". */
   int (*run_launches)(void* ctx, int kind, const ct_config* cfg, int n, double* elapsed_ms);
+  /* Board power limit (the paper's nvml_pwr_limit tunable, Section IV-C),
+     in mW: set, restore the device's default, and the allowed range. */
+  int (*set_power_limit)(void* ctx, int mw);
+  int (*reset_power_limit)(void* ctx);
+  int (*power_limit_range)(void* ctx, int* min_mw, int* max_mw, int* default_mw);
 } ct_platform_ops;
 
 /* One reading of the platform's sensors (the observer record of Section
@@ -289,6 +298,7 @@ typedef struct {
   double wall_s;           /* host seconds spent on this point              */
   int n_launches;          /* launches timed                                */
   int flags;               /* CT_REC_*                                      */
+  double power_limit_w;    /* requested board power limit, 0 = the default  */
 } ct_record;
 
 /*
@@ -448,6 +458,23 @@ int ct_tune(const ct_problem* p, const ct_config* space, int n_space, const int*
             int n_clocks, const ct_tune_options* opt, void* stream, ct_record* records, int cap,
             int* n_records, int* best_index);
 
+/*
+ * Power capping instead of clock locking (Section IV-C compares the two):
+ * exhaustive search of `space` x board power limits (mW, within the device's
+ * range) at default clocks, limit-major, each limit set once and the
+ * default restored before returning, on every path.  Records carry the limit
+ * in power_limit_w (clock_mhz_req = 0); a power cap that lowered the clock
+ * shows as CT_REC_THROTTLED.  Cache, records, capacity and selection as
+ * ct_tune; with fallback_default_clocks a refused limit gives one pass at
+ * the default limit flagged CT_REC_DEFAULT_CLOCKS.
+ */
+int ct_tune_power_limits(const ct_problem* p, const ct_config* space, int n_space,
+                         const int* limits_mw, int n_limits, const ct_tune_options* opt,
+                         void* stream, ct_record* records, int cap, int* n_records,
+                         int* best_index);
+/* The device's power-limit range and default (mW), from the platform table. */
+int ct_power_limit_range(int* min_mw, int* max_mw, int* default_mw);
+
 /* The selection rule of ct_tune over given records, optionally restricted to
    records whose requested clock is in clocks[] (n_clocks > 0). */
 int ct_select_best(const ct_record* recs, int n, int objective, const int* clocks,
@@ -549,8 +576,13 @@ typedef struct {
 } ct_batch_item;
 
 typedef struct {
-  int block_x[2][18]; /* [size class][k]: 16, 32, 64 or 128 (block_y = 256/block_x) */
+  int block_x[2][18]; /* [size class][k]: 16, 32, 64 or 128, <= the class's CTA size
+                         (block_y = CTA size / block_x)                      */
   int tile_y[2][18];  /* [size class][k]: 1, 2 or 4; also 8 for k <= 3     */
+  int class_threads[3]; /* CTA size of the filter-side classes 1-7, 9-11,
+                           13-17: 64, 128 or 256 (0: 256)                    */
+  int claim_items[3];   /* work items (consecutive tiles) per claim of the
+                           persistent CTAs, per class: 1..8 (0: 2, 1, 1)     */
 } ct_batch_tiles;
 
 typedef struct {
@@ -662,7 +694,29 @@ typedef struct {
   int plain;             /* 1: one plain kernel per request (comparison)    */
   int use_tiles;         /* 1: per-bucket tiles from `tiles`                */
   ct_batch_tiles tiles;
+  int trace_cap;         /* > 0: keep a timeline of the last trace_cap
+                            batches (ct_server_trace_get); 0: none           */
 } ct_server_options;
+
+/* One batch of the worker's timeline (host steady-clock seconds). */
+typedef struct {
+  double t_dispatch;     /* the worker took the batch                       */
+  double dispatch_s;     /* host time enqueueing it: copies, plan, launches */
+  double plan_s;         /* of which: image table and launch plan           */
+  double t_done;         /* the worker saw its completion event             */
+  double oldest_wait_s;  /* its oldest request: submission to t_dispatch    */
+  double loop_gap_s;     /* longest pause between two worker iterations
+                            since the previous batch was taken              */
+  int n_requests;
+  int slot;              /* stream slot it ran on                           */
+  int queued;            /* requests waiting for admission at t_dispatch    */
+  int busy_slots;        /* other batches in flight at t_dispatch           */
+  double h2d_ms;         /* device time (CUDA events on the batch's stream):
+                            input copies                                     */
+  double kernels_ms;     /* the batch's kernels                             */
+  double d2h_ms;         /* output copies                                   */
+  double bytes_in, bytes_out;  /* copied in / out                            */
+} ct_server_trace_entry;
 
 typedef struct {
   long long submitted, completed, rejected;
@@ -690,6 +744,14 @@ int ct_server_drain(ct_server* sv, double timeout_s);
 int ct_server_stats_get(ct_server* sv, int reset, ct_server_stats* out);
 /* Finish every queued request, stop the worker and free the server. */
 int ct_server_destroy(ct_server* sv);
+/*
+ * The timeline of the last completed batches (at most trace_cap, oldest
+ * first): *n receives the count; CT_ENOMEM if it exceeds cap (the count is
+ * still written); CT_ENOTSUP if the server keeps no timeline.  A diagnostic:
+ * where a request's latency went (waiting for admission or a free slot,
+ * enqueueing on the worker, device and copies, pauses of the worker).
+ */
+int ct_server_trace_get(ct_server* sv, ct_server_trace_entry* out, int cap, int* n);
 
 
 /* ---- analyses of tuning records (Sections IV-A, IV-B) ------------------- */

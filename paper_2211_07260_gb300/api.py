@@ -44,6 +44,7 @@ class CtDeviceInfo(ctypes.Structure):
 
 
 CT_UNIT_CONV, CT_UNIT_FMA, CT_UNIT_COPY = 0, 1, 2
+CT_THR_SW_POWER_CAP, CT_THR_HW_SLOWDOWN, CT_THR_SW_THERMAL, CT_THR_HW_THERMAL = 0x4, 0x8, 0x20, 0x40
 CT_STEER_UNION = 3
 CT_OBJ_TIME, CT_OBJ_ENERGY, CT_OBJ_GFLOPS_PER_W = 0, 1, 2
 CT_SPACE_BASIC, CT_SPACE_FULL = 0, 1
@@ -59,6 +60,8 @@ _FN_CLOCKS = ctypes.CFUNCTYPE(c_int, c_void_p, ctypes.POINTER(c_int), c_int, cty
 _FN_LOCK = ctypes.CFUNCTYPE(c_int, c_void_p, c_int)
 _FN_RESET = ctypes.CFUNCTYPE(c_int, c_void_p)
 _FN_NOW = ctypes.CFUNCTYPE(c_double, c_void_p)
+_FN_PLRANGE = ctypes.CFUNCTYPE(c_int, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                               ctypes.POINTER(c_int))
 _FN_RUN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int, ctypes.POINTER(CtConfig), c_int,
                            ctypes.POINTER(c_double))
 
@@ -68,7 +71,9 @@ class CtPlatformOps(ctypes.Structure):
                 ("sm_clock_mhz", _FN_UINT), ("throttle_reasons", _FN_ULL),
                 ("temperature_c", _FN_UINT), ("other_processes", _FN_INTP),
                 ("supported_sm_clocks", _FN_CLOCKS), ("lock_sm_clock", _FN_LOCK),
-                ("reset_sm_clock", _FN_RESET), ("now_s", _FN_NOW), ("run_launches", _FN_RUN)]
+                ("reset_sm_clock", _FN_RESET), ("now_s", _FN_NOW), ("run_launches", _FN_RUN),
+                ("set_power_limit", _FN_LOCK), ("reset_power_limit", _FN_RESET),
+                ("power_limit_range", _FN_PLRANGE)]
 
 
 class CtMeasureOptions(ctypes.Structure):
@@ -81,7 +86,8 @@ class CtRecord(ctypes.Structure):
                 ("t_s", c_double), ("energy_j", c_double), ("power_w_mean", c_double),
                 ("power_w_median", c_double), ("energy_j_median_power", c_double),
                 ("gflops", c_double), ("gflops_per_j", c_double), ("temp_c", c_double),
-                ("wall_s", c_double), ("n_launches", c_int), ("flags", c_int)]
+                ("wall_s", c_double), ("n_launches", c_int), ("flags", c_int),
+                ("power_limit_w", c_double)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cfg"}
@@ -204,6 +210,9 @@ _SIGS = {
     "ct_space": (c_int, [c_int, c_void_p, c_int, c_void_p]),
     "ct_tune": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                         c_int, c_void_p, c_void_p]),
+    "ct_tune_power_limits": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
+                                     c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "ct_power_limit_range": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ct_select_best": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_void_p]),
     "ct_microbench_launch": (c_int, [c_int, c_void_p, c_void_p]),
     "ct_measure_microbench": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
@@ -227,6 +236,7 @@ _SIGS = {
     "ct_server_drain": (c_int, [c_void_p, c_double]),
     "ct_server_stats_get": (c_int, [c_void_p, c_int, c_void_p]),
     "ct_server_destroy": (c_int, [c_void_p]),
+    "ct_server_trace_get": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "ct_read_sensors": (c_int, [c_void_p]),
     "ct_tuning_methods": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "ct_pareto_front": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p]),
@@ -569,6 +579,34 @@ def tune(inp, filt, out, out_h, out_w, cfgs=None, clocks=None, opts=None, stream
     return [recs[i].to_dict() for i in range(n.value)], best.value
 
 
+def tune_power_limits(inp, filt, out, out_h, out_w, limits_w, cfgs=None, opts=None, stream=None,
+                      in_pitch=None, out_pitch=None):
+    """Exhaustive search over configurations x board power limits in watts
+    (ct_tune_power_limits).  Returns (records, best_index)."""
+    p, f = make_problem(inp, filt, out, out_h, out_w, in_pitch, out_pitch)
+    sp, ns = _space_array(cfgs)
+    lim = np.ascontiguousarray([int(round(w * 1000)) for w in limits_w], dtype=np.int32)
+    o = opts or tune_options()
+    n_space = ns if sp is not None else len(space(CT_SPACE_BASIC))
+    cap = n_space * max(1, lim.size)
+    recs = (CtRecord * cap)()
+    n = c_int(0)
+    best = c_int(-1)
+    _check(lib().ct_tune_power_limits(ctypes.byref(p), sp, ns,
+                                      lim.ctypes.data if lim.size else None, lim.size,
+                                      ctypes.byref(o), c_void_p(stream_handle(stream)), recs, cap,
+                                      ctypes.byref(n), ctypes.byref(best)), "ct_tune_power_limits")
+    return [recs[i].to_dict() for i in range(n.value)], best.value
+
+
+def power_limit_range():
+    """(min, max, default) board power limit in watts."""
+    lo, hi, de = c_int(0), c_int(0), c_int(0)
+    _check(lib().ct_power_limit_range(ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(de)),
+           "ct_power_limit_range")
+    return lo.value / 1000.0, hi.value / 1000.0, de.value / 1000.0
+
+
 def select_best(records, objective="energy", clocks=None) -> int:
     arr = (CtRecord * len(records))()
     for i, r in enumerate(records):
@@ -576,7 +614,7 @@ def select_best(records, objective="energy", clocks=None) -> int:
             if k == "cfg":
                 arr[i].cfg = Config(*r["cfg"]).to_c()
             else:
-                setattr(arr[i], k, r[k])
+                setattr(arr[i], k, r.get(k, 0))
     ck = np.ascontiguousarray(clocks if clocks is not None else [], dtype=np.int32)
     best = c_int(-1)
     obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
@@ -654,23 +692,55 @@ class CtBatchItem(ctypes.Structure):
 
 
 class CtBatchTiles(ctypes.Structure):
-    _fields_ = [("block_x", (c_int * 18) * 2), ("tile_y", (c_int * 18) * 2)]
+    _fields_ = [("block_x", (c_int * 18) * 2), ("tile_y", (c_int * 18) * 2),
+                ("class_threads", c_int * 3), ("claim_items", c_int * 3)]
 
     def to_dict(self) -> dict:
+        """{(size class, k): (block_x, tile_y)} plus {("threads", filter-side
+        class): CTA size} and {("claim", filter-side class): items per claim}
+        for the classes where they are set."""
         out = {}
         for cls in (0, 1):
             for k in range(18):
                 if self.block_x[cls][k]:
                     out[(cls, k)] = (self.block_x[cls][k], self.tile_y[cls][k])
+        for c in range(3):
+            if self.class_threads[c]:
+                out[("threads", c)] = self.class_threads[c]
+            if self.claim_items[c]:
+                out[("claim", c)] = self.claim_items[c]
         return out
 
     @classmethod
     def from_dict(cls, d: dict) -> "CtBatchTiles":
         t = cls()
-        for (c, k), (bx, ty) in d.items():
-            t.block_x[c][k] = bx
-            t.tile_y[c][k] = ty
+        for key, val in d.items():
+            if key[0] == "threads":
+                t.class_threads[int(key[1])] = int(val)
+            elif key[0] == "claim":
+                t.claim_items[int(key[1])] = int(val)
+            else:
+                c, k = key
+                t.block_x[c][k], t.tile_y[c][k] = val
         return t
+
+
+def tiles_from_json(raw: dict) -> dict:
+    """Tiles dict from its JSON form ({"c,k": [bx, ty], "threads,c": n,
+    "claim,c": n})."""
+    out = {}
+    for key, val in raw.items():
+        a, b = key.split(",")
+        if a in ("threads", "claim"):
+            out[(a, int(b))] = int(val)
+        else:
+            out[(int(a), int(b))] = tuple(val)
+    return out
+
+
+def tiles_to_json(tiles: dict) -> dict:
+    return {f"{a},{b}": (val if a in ("threads", "claim") else list(val))
+            for (a, b), val in tiles.items()}
 
 
 class CtBatchStats(ctypes.Structure):
@@ -738,10 +808,13 @@ class Batch:
         self.destroy()
 
 
-def batch_tune(entries, objective="energy", opts=None, stream=None):
-    """Per-bucket tiles by the tuner (ct_batch_tune): (tiles dict, records)."""
+def batch_tune(entries, objective="energy", opts=None, stream=None, class_threads=None):
+    """Per-bucket tiles by the tuner (ct_batch_tune): (tiles dict, records).
+    class_threads: optional CTA size per filter-side class to tune with."""
     items, keep = batch_items(entries)
     t = CtBatchTiles()
+    for c, n in enumerate(class_threads or ()):
+        t.class_threads[c] = int(n)
     cap = 12 * 2 * 18
     recs = (CtRecord * cap)()
     n = c_int(0)
@@ -757,7 +830,15 @@ def batch_tune(entries, objective="energy", opts=None, stream=None):
 class CtServerOptions(ctypes.Structure):
     _fields_ = [("n_streams", c_int), ("max_batch", c_int), ("pool_bytes", ctypes.c_longlong),
                 ("max_wait_s", c_double), ("plain", c_int), ("use_tiles", c_int),
-                ("tiles", CtBatchTiles)]
+                ("tiles", CtBatchTiles), ("trace_cap", c_int)]
+
+
+class CtServerTraceEntry(ctypes.Structure):
+    _fields_ = [("t_dispatch", c_double), ("dispatch_s", c_double), ("plan_s", c_double),
+                ("t_done", c_double), ("oldest_wait_s", c_double), ("loop_gap_s", c_double),
+                ("n_requests", c_int), ("slot", c_int), ("queued", c_int),
+                ("busy_slots", c_int), ("h2d_ms", c_double), ("kernels_ms", c_double),
+                ("d2h_ms", c_double), ("bytes_in", c_double), ("bytes_out", c_double)]
 
 
 class CtServerStats(ctypes.Structure):
@@ -773,10 +854,10 @@ class Server:
     to submit() must stay alive until the request completes."""
 
     def __init__(self, n_streams=4, max_batch=64, pool_bytes=8 << 30, max_wait_s=200e-6,
-                 plain=False, tiles: dict | None = None):
+                 plain=False, tiles: dict | None = None, trace_cap=0):
         o = CtServerOptions(n_streams, max_batch, pool_bytes, max_wait_s, int(bool(plain)),
                             1 if tiles else 0, CtBatchTiles.from_dict(tiles) if tiles
-                            else CtBatchTiles())
+                            else CtBatchTiles(), int(trace_cap))
         self._h = c_void_p(0)
         _check(lib().ct_server_create(ctypes.byref(o), ctypes.byref(self._h)), "ct_server_create")
         self._keep = {}
@@ -803,6 +884,18 @@ class Server:
                "ct_server_stats_get")
         return {k: getattr(st, k) for k, _ in CtServerStats._fields_}
 
+    def trace(self) -> list:
+        """The timeline of the last completed batches (ct_server_trace_get)."""
+        n = c_int(0)
+        rc = lib().ct_server_trace_get(self._h, None, 0, ctypes.byref(n))
+        if rc not in (CT_OK, CT_ENOMEM):
+            _check(rc, "ct_server_trace_get")
+        buf = (CtServerTraceEntry * max(1, n.value))()
+        _check(lib().ct_server_trace_get(self._h, buf, n.value, ctypes.byref(n)),
+               "ct_server_trace_get")
+        return [{k: getattr(buf[i], k) for k, _ in CtServerTraceEntry._fields_}
+                for i in range(n.value)]
+
     def close(self):
         if self._h:
             lib().ct_server_destroy(self._h)
@@ -827,7 +920,7 @@ def _record_array(records):
             if k == "cfg":
                 arr[i].cfg = Config(*r["cfg"]).to_c()
             else:
-                setattr(arr[i], k, r[k])
+                setattr(arr[i], k, r.get(k, 0))
     return arr
 
 

@@ -21,14 +21,14 @@ namespace convtune {
 
 template <int KK>
 __device__ __forceinline__ void run_tile_k(const BatchArgs& a, const BatchImage& im, int t,
-                                           float* smem) {
-  if (im.ty == 1) batch_tile<KK, 1>(a, im, t, smem);
-  else if (im.ty == 2) batch_tile<KK, 2>(a, im, t, smem);
+                                           const float* buf, const float* sfilt) {
+  if (im.ty == 1) batch_tile<KK, 1>(a, im, t, buf, sfilt);
+  else if (im.ty == 2) batch_tile<KK, 2>(a, im, t, buf, sfilt);
   else if constexpr (KK <= kBatchMaxK8) {
-    if (im.ty == 8) batch_tile<KK, 8>(a, im, t, smem);
-    else batch_tile<KK, 4>(a, im, t, smem);
+    if (im.ty == 8) batch_tile<KK, 8>(a, im, t, buf, sfilt);
+    else batch_tile<KK, 4>(a, im, t, buf, sfilt);
   } else {
-    batch_tile<KK, 4>(a, im, t, smem);
+    batch_tile<KK, 4>(a, im, t, buf, sfilt);
   }
 }
 
@@ -36,12 +36,12 @@ __device__ __forceinline__ void run_tile_k(const BatchArgs& a, const BatchImage&
 // the host did not split correctly) only raises the status bit.
 template <int CLS>
 __device__ __forceinline__ void run_tile(const BatchArgs& a, const BatchImage& im, int t,
-                                         float* smem, unsigned* status) {
+                                         const float* buf, const float* sfilt, unsigned* status) {
   switch (im.k) {
 #define CT_BATCH_CASE(KK)                                                        \
   case KK:                                                                       \
     if constexpr (batch_class_of(KK) == CLS) {                                   \
-      run_tile_k<KK>(a, im, t, smem);                                            \
+      run_tile_k<KK>(a, im, t, buf, sfilt);                                      \
       return;                                                                    \
     }                                                                            \
     break;
@@ -61,60 +61,186 @@ __device__ __forceinline__ void run_tile(const BatchArgs& a, const BatchImage& i
   if (threadIdx.x == 0) atomicOr(status, kStatusBadItem);
 }
 
-// resident CTAs per SM each class kernel is compiled for (registers <= 64,
-// 85, 128 per thread)
-__host__ __device__ constexpr int batch_class_min_ctas(int cls) { return cls == 0 ? 4 : (cls == 1 ? 3 : 2); }
+// resident CTAs per SM each class kernel is compiled for (registers <= 80,
+// 80, 128 per thread; sides 1-7 measured 164 -> 148 us with 80 registers
+// and 3 CTAs instead of 64 and 4, whose spills cost more than the fourth CTA
+// gave)
+__host__ __device__ constexpr int batch_class_min_ctas(int cls) { return cls == 2 ? 2 : 3; }
+
+// largest filter side of a class (its shared-memory tap area)
+__host__ __device__ constexpr int batch_class_max_k(int cls) { return cls == 0 ? 7 : (cls == 1 ? 11 : 17); }
+
+// Images whose first work items a CTA keeps in shared memory for the lookup
+// (larger launches search the table in global memory).
+constexpr int kBatchFirstCache = 512;
+
+// Claim state, touched by lane 0 of warp 0 only.
+struct BatchClaimState {
+  unsigned cur, end;     // items [cur, end) of the current chunk
+  long long first, last;  // table items [first, last) of image `img`
+  int img;
+};
+
+// Lane 0 of warp 0: the launch item after the current one (taking the
+// prefetched chunk, and prefetching the next, when the current chunk is
+// used up), or n_items past the end.
+__device__ __forceinline__ unsigned batch_next_item(const BatchArgs& a, BatchClaimState* c,
+                                                    unsigned* next_chunk) {
+  if (c->cur >= c->end) {
+    const unsigned long long lo = (unsigned long long)*next_chunk * a.claim_items;
+    if (lo >= (unsigned long long)a.n_items) return (unsigned)a.n_items;
+    c->cur = (unsigned)lo;
+    const unsigned long long hi = lo + a.claim_items;
+    c->end = (unsigned)(hi < (unsigned long long)a.n_items ? hi : (unsigned long long)a.n_items);
+    *next_chunk = atomicAdd(a.counter, 1u);
+  }
+  return c->cur++;
+}
+
+// Lane 0 of warp 0: the image and tile of launch item w, or -1 past the end
+// of the launch's items and -2 for an item outside its image.  The range of
+// the last image found is kept; otherwise a binary search over first_item
+// (from shared memory when the launch has at most kBatchFirstCache images).
+__device__ __forceinline__ int batch_resolve(const BatchArgs& a, unsigned w, BatchClaimState* c,
+                                             const long long* s_first, long long* tile) {
+  if ((long long)w >= a.n_items) return -1;
+  const long long gw = a.item_base + (long long)w;
+  if (gw < c->first || gw >= c->last) {
+    const bool cached = a.n_images <= kBatchFirstCache;
+    int lo = 0, hi = a.n_images - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if ((cached ? s_first[mid] : a.images[mid].first_item) <= gw) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchImage& im = a.images[lo];
+    c->img = lo;
+    c->first = im.first_item;
+    c->last = im.first_item + (long long)im.tiles_x * im.tiles_y;
+    if (gw < c->first || gw >= c->last) return -2;
+  }
+  *tile = gw - c->first;
+  return c->img;
+}
+
+// Warp 0: slot `dst` of the work-item ring describes item w (its image entry
+// copied from the table, or from slot `prev` when the image is the same).
+__device__ __forceinline__ void batch_fill_slot(const BatchArgs& a, unsigned w, int dst, int prev,
+                                                BatchClaimState* c, const long long* s_first,
+                                                BatchImage* s_desc, long long* s_tile,
+                                                int* s_img) {
+  const int lane = threadIdx.x & 31;
+  int img = 0;
+  if (lane == 0) {
+    long long tl = 0;
+    img = batch_resolve(a, w, c, s_first, &tl);
+    s_img[dst] = img;
+    s_tile[dst] = tl;
+  }
+  img = __shfl_sync(0xffffffffu, img, 0);
+  if (img >= 0) {
+    const uint2* src = prev >= 0 && s_img[prev] == img
+                           ? reinterpret_cast<const uint2*>(&s_desc[prev])
+                           : reinterpret_cast<const uint2*>(a.images + img);
+    reinterpret_cast<uint2*>(&s_desc[dst])[lane] = src[lane];
+  }
+  __syncwarp();
+}
 
 template <int CLS>
 __global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
     batched_conv_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* smem = reinterpret_cast<float*>(smem_raw);
-  __shared__ long long s_item;
-  __shared__ int s_img;
-  // thread 0 claims each work item one tile ahead (the atomic's round trip
-  // overlaps the current tile) and remembers the last item's image (most
-  // items a CTA claims in a row lie in the same large image)
-  long long next = 0;
-  int last_img = 0;
-  if (threadIdx.x == 0) next = (long long)atomicAdd(a.counter, 1u);
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const long long w = next;
-      int img = -1;
-      if (w < a.n_items) {
-        next = (long long)atomicAdd(a.counter, 1u);
-        const long long gw = a.item_base + w;
-        const BatchImage& c = a.images[last_img];
-        if (gw >= c.first_item && gw < c.first_item + (long long)c.tiles_x * c.tiles_y) {
-          img = last_img;
-        } else {
-          // last image whose first item is <= the table item
-          int lo = 0, hi = a.n_images - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (a.images[mid].first_item <= gw) lo = mid;
-            else hi = mid - 1;
-          }
-          img = lo;
-        }
-        last_img = img;
+  constexpr int kFilt = batch_filt_floats(batch_class_max_k(CLS));
+  float* const sfilt = reinterpret_cast<float*>(smem_raw);
+  float* const bufs = sfilt + kFilt;  // two staging buffers of a.buf_floats
+  __shared__ __align__(8) uint64_t mbar[2];
+  // Work-item ring: item i's image entry (copied from the table), image index
+  // and tile sit in slot i % 3.  Warp 0 fills slot (i+2) % 3 and lane 0
+  // starts item i+1's input copy into staging buffer (i+1) % 2 at the start
+  // of item i; the CTA then computes item i.  Claims run a chunk ahead.
+  __shared__ __align__(128) BatchImage s_desc[3];
+  __shared__ long long s_tile[3];
+  __shared__ int s_img[3];
+  __shared__ long long s_first[kBatchFirstCache];
+  __shared__ BatchClaimState s_claim;
+  const int tid = threadIdx.x;
+  const bool warp0 = tid < 32;
+  unsigned next_chunk = 0;  // lane 0: the chunk claimed ahead
+  if (a.n_images <= kBatchFirstCache)
+    for (int q = tid; q < a.n_images; q += blockDim.x) s_first[q] = a.images[q].first_item;
+  if (tid == 0) {
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    mbar_init_fence();
+    s_claim.cur = s_claim.end = 0;
+    s_claim.first = s_claim.last = -1;
+    s_claim.img = 0;
+    next_chunk = atomicAdd(a.counter, 1u);
+  }
+  __syncthreads();
+  if (warp0) {
+    // prologue: items 0 and 1 described, item 0's copy started
+    for (int q = 0; q < 2; ++q) {
+      unsigned w = 0;
+      if (tid == 0) w = batch_next_item(a, &s_claim, &next_chunk);
+      batch_fill_slot(a, w, q, q - 1, &s_claim, s_first, s_desc, s_tile, s_img);
+    }
+    if (tid == 0 && s_img[0] >= 0 && s_desc[0].use_tma)
+      batch_issue_tma(&s_desc[0], a.images + s_img[0], (int)s_tile[0], bufs, &mbar[0]);
+  }
+  __syncthreads();
+  unsigned phase = 0;  // bit b: parity of mbar[b]'s next phase
+  for (int i = 0;; ++i) {
+    const int c3 = i % 3, n3 = (i + 1) % 3, f3 = (i + 2) % 3;
+    const int b = i & 1;
+    const int img = s_img[c3];
+    if (img == -1) break;
+    float* const buf = bufs + b * a.buf_floats;
+    if (warp0) {
+      // item i+1's copy (into the buffer item i-1 used: every thread passed
+      // the barrier after computing it), then item i+2 into ring slot f3
+      // (it held item i-1)
+      if (tid == 0 && s_img[n3] >= 0 && s_desc[n3].use_tma)
+        batch_issue_tma(&s_desc[n3], a.images + s_img[n3], (int)s_tile[n3],
+                        bufs + (b ^ 1) * a.buf_floats, &mbar[b ^ 1]);
+      unsigned w = (unsigned)a.n_items;
+      if (tid == 0 && s_img[n3] != -1) w = batch_next_item(a, &s_claim, &next_chunk);
+      batch_fill_slot(a, w, f3, n3, &s_claim, s_first, s_desc, s_tile, s_img);
+    }
+    bool ok = true;
+    if (img >= 0) {
+      const BatchImage& im = s_desc[c3];
+      const int tl = (int)s_tile[c3];  // tiles of one image fit 32 bits
+      const bool param_taps = im.tap_off >= 0;  // CTA-uniform, like use_tma
+      if (!param_taps) {
+        const int kp = (im.k + 3) / 4 * 4;
+        for (int q = tid; q < im.k * kp; q += blockDim.x) sfilt[q] = im.filt[q];
       }
-      s_item = w;
-      s_img = img;
+      if (im.use_tma) {
+        ok = mbar_wait(&mbar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        if (!param_taps) __syncthreads();
+      } else {
+        batch_stage_cp_async(im, tl, buf);
+        __syncthreads();
+      }
+      if (ok) run_tile<CLS>(a, im, tl, buf, sfilt, a.status);
+    } else if (tid == 0) {
+      atomicOr(a.status, kStatusBadItem);
     }
-    __syncthreads();
-    const long long w = s_item;
-    const int img = s_img;
-    __syncthreads();  // s_item / s_img are rewritten only after this point
-    if (w >= a.n_items) break;
-    const BatchImage& im = a.images[img];
-    const long long tl = a.item_base + w - im.first_item;
-    if (tl < 0 || tl >= (long long)im.tiles_x * im.tiles_y) {
-      if (threadIdx.x == 0) atomicOr(a.status, kStatusBadItem);
-      continue;
+    // the buffer and the ring slots are rewritten only after this point
+    if (__syncthreads_or(!ok)) {
+      // a copy never completed: report it, give the copies still in flight
+      // (this item's, and the next item's if it has one) a bounded wait to
+      // land, and stop this CTA
+      if (tid == 0) {
+        atomicOr(a.status, kStatusTmaTimeout);
+        mbar_wait(&mbar[b], ((phase >> b) & 1u) ^ 1u);
+        if (s_img[n3] >= 0 && s_desc[n3].use_tma) mbar_wait(&mbar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+      }
+      return;
     }
-    run_tile<CLS>(a, im, (int)tl, smem, a.status);  // tiles of one image fit in 32 bits
   }
 }
 
@@ -132,18 +258,27 @@ constexpr size_t kBatchBranches = 8;  // parallel branches of a captured batch g
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
-size_t batch_smem_bytes(int k, int bx, int ty) {
-  const int kp = round_up(k, 4);
-  const int filt = round_up(k * kp, 32);
-  const int by = kBatchThreads / bx;
-  const int tile_w = round_up(bx * kBatchTileX + k - 1, 4);
-  const int tile_h = batch_subtiles(k) * by * ty + k - 1;
-  return sizeof(float) * (size_t)(filt + tile_w * tile_h);
+// Dynamic shared memory of a class launch whose largest staging buffer is
+// buf_floats: the class's shared-memory tap area and two buffers.
+size_t batch_launch_smem(int cls, int buf_floats) {
+  return sizeof(float) * (size_t)(batch_filt_floats(batch_class_max_k(cls)) + 2 * buf_floats);
 }
 
-bool valid_tile(int bx, int ty, int k) {
-  return (bx == 16 || bx == 32 || bx == 64 || bx == 128) &&
+bool valid_tile(int bx, int ty, int k, int threads) {
+  return (bx == 16 || bx == 32 || bx == 64 || bx == 128) && bx <= threads &&
          (ty == 1 || ty == 2 || ty == 4 || (ty == 8 && k <= kBatchMaxK8));
+}
+
+// CTA size of filter side k's class launch.
+int class_threads(const ct_batch_tiles* tiles, int k) {
+  const int t = tiles ? tiles->class_threads[batch_class_of(k)] : 0;
+  return batch_valid_threads(t) ? t : kBatchThreads;
+}
+
+// Work items per claim of filter side k's class launch.
+int class_claim(const ct_batch_tiles* tiles, int k) {
+  const int c = tiles ? tiles->claim_items[batch_class_of(k)] : 0;
+  return c >= 1 && c <= 8 ? c : batch_default_claim(batch_class_of(k));
 }
 
 int size_class(int h, int w) { return (long long)h * w >= 512LL * 512LL ? 1 : 0; }
@@ -186,20 +321,25 @@ int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPla
   auto finish = [&](BatchClassLaunch& L) -> int {
     L.n = L.hi - L.lo;
     if (L.n == 0) return CT_OK;
-    size_t buf = 0;
+    int buf = 32;
     for (int q = L.lo; q < L.hi; ++q) {
       L.items += (long long)table[q].tiles_x * table[q].tiles_y;
-      buf = std::max(buf, batch_smem_bytes(table[q].k, table[q].bx, table[q].ty));
+      buf = std::max(buf, table[q].g.buf_floats);
     }
     L.item_base = table[L.lo].first_item;
-    L.smem = std::max<size_t>(buf, 16);
+    L.threads = table[L.lo].threads;
+    L.claim = table[L.lo].claim;
+    for (int q = L.lo; q < L.hi; ++q)  // one CTA size and claim size per launch
+      if (table[q].threads != L.threads || table[q].claim != L.claim) return CT_EINVAL;
+    L.buf_floats = buf;
+    L.smem = batch_launch_smem(L.cls, buf);
     cudaFuncAttributes fa;
     cudaError_t e2 = cudaFuncGetAttributes(&fa, batched_kernel_fn(L.cls));
     if (e2 != cudaSuccess) return cuda_status(e2);
     if (L.smem + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
     int per_sm = 0;
     if ((e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_fn(L.cls),
-                                                            kBatchThreads, L.smem)) != cudaSuccess)
+                                                            L.threads, L.smem)) != cudaSuccess)
       return cuda_status(e2);
     if (per_sm < 1) return CT_ECONFIG;
     L.grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sms, L.items));
@@ -268,10 +408,12 @@ int enqueue_batch_plan(const BatchPlan& plan, const BatchImage* d_table, unsigne
     a.item_base = L.item_base;
     a.counter = counters + l;
     a.status = status;
+    a.buf_floats = L.buf_floats;
+    a.claim_items = (unsigned)L.claim;
     if (!L.taps.empty()) memcpy(a.w, L.taps.data(), sizeof(float) * L.taps.size());
-    if (L.cls == 0) batched_conv_kernel<0><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
-    else if (L.cls == 1) batched_conv_kernel<1><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
-    else batched_conv_kernel<2><<<L.grid, kBatchThreads, L.smem, ls>>>(a);
+    if (L.cls == 0) batched_conv_kernel<0><<<L.grid, L.threads, L.smem, ls>>>(a);
+    else if (L.cls == 1) batched_conv_kernel<1><<<L.grid, L.threads, L.smem, ls>>>(a);
+    else batched_conv_kernel<2><<<L.grid, L.threads, L.smem, ls>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
   }
   for (int b = 0; b < nb; ++b)
@@ -346,7 +488,7 @@ int enqueue_plain(ct_batch* b, cudaStream_t s) {
     p.out_w = it.out_w;
     ct_config c;
     c.block_x = im.bx;
-    c.block_y = kBatchThreads / im.bx;
+    c.block_y = im.threads / im.bx;
     c.tile_x = kBatchTileX;
     c.tile_y = std::min(im.ty, 4);  // (the single-image kernel's tiles are at most 4 high)
     c.staging = CT_STAGE_SMEM;
@@ -369,35 +511,9 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
     if (it.out_h < 0 || it.out_w < 0) return CT_EINVAL;
     b->taps[i].assign(it.filt, it.filt + it.k * it.k);
     if (it.out_h == 0 || it.out_w == 0) continue;
-    if (!it.in || !it.out) return CT_EINVAL;
-    if (it.in_pitch < (long)it.out_w + it.k - 1 || it.out_pitch < it.out_w) return CT_EINVAL;
-    if ((long long)it.out_w + it.k > (1LL << 30) || (long long)it.out_h + it.k > (1LL << 30))
-      return CT_EINVAL;
     BatchImage im;
-    memset(&im, 0, sizeof(im));
-    im.tap_off = -1;
-    im.in = it.in;
-    im.out = it.out;
-    im.in_pitch = it.in_pitch;
-    im.out_pitch = it.out_pitch;
-    im.in_h = it.out_h + it.k - 1;
-    im.in_w = it.out_w + it.k - 1;
-    im.out_h = it.out_h;
-    im.out_w = it.out_w;
-    im.k = it.k;
-    const int cls = size_class(it.out_h, it.out_w);
-    int bx = 32, ty = 2;
-    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k], it.k)) {
-      bx = tiles->block_x[cls][it.k];
-      ty = tiles->tile_y[cls][it.k];
-    }
-    im.bx = bx;
-    im.ty = ty;
-    const bool aligned = (uintptr_t)it.in % 16 == 0 && it.in_pitch % 4 == 0 &&
-                         (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
-    im.vw = aligned ? 4 : 1;
-    im.tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
-    im.tiles_y = (it.out_h + batch_item_rows(it.k, bx, ty) - 1) / batch_item_rows(it.k, bx, ty);
+    const int rc = batch_image_from_item(it, tiles, &im);
+    if (rc != CT_OK) return rc;
     imgs.push_back(im);
     order.push_back(i);
     b->flop += 2.0 * it.k * it.k * (double)it.out_h * it.out_w;
@@ -570,7 +686,16 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
                   ct_record* records, int cap, int* n_records) {
   if (!items || n <= 0 || !tiles || !n_records) return CT_EINVAL;
   if (objective < CT_OBJ_TIME || objective > CT_OBJ_GFLOPS_PER_W) return CT_EINVAL;
+  // the caller's class CTA sizes and claim sizes (0: default) are kept and
+  // tuned with
+  int cls_threads[kBatchClasses], cls_claim[kBatchClasses];
+  for (int c = 0; c < kBatchClasses; ++c) {
+    cls_threads[c] = batch_valid_threads(tiles->class_threads[c]) ? tiles->class_threads[c] : 0;
+    cls_claim[c] = tiles->claim_items[c] >= 1 && tiles->claim_items[c] <= 8 ? tiles->claim_items[c] : 0;
+  }
   memset(tiles, 0, sizeof(*tiles));
+  memcpy(tiles->class_threads, cls_threads, sizeof(cls_threads));
+  memcpy(tiles->claim_items, cls_claim, sizeof(cls_claim));
   const ct_measure_options mo = resolve_options(opt);
   const ct_platform_ops ops = platform_ops();
   // representative image of each bucket: the median output area
@@ -603,6 +728,9 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
           const int ty = tys[qt];
           ct_batch_tiles t;
           memset(&t, 0, sizeof(t));
+          memcpy(t.class_threads, cls_threads, sizeof(cls_threads));
+          memcpy(t.claim_items, cls_claim, sizeof(cls_claim));
+          if (bx > class_threads(&t, k)) continue;  // wider than the CTA
           t.block_x[cls][k] = bx;
           t.tile_y[cls][k] = ty;
           ct_batch* b = nullptr;
@@ -617,7 +745,7 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
           ct_batch_destroy(b);
           if (rc != CT_OK) return rc;
           r.cfg.block_x = bx;
-          r.cfg.block_y = kBatchThreads / bx;
+          r.cfg.block_y = class_threads(&t, k) / bx;
           r.cfg.tile_x = kBatchTileX;
           r.cfg.tile_y = ty;
           r.cfg.staging = CT_STAGE_SMEM;
@@ -757,30 +885,8 @@ extern "C" int ct_batch_run_noalloc(const ct_batch_item* items, int n,
   for (int q = 0; q < m; ++q) {
     const ct_batch_item& it = items[idx[q]];
     BatchImage& im = hb.table[q];
-    memset(&im, 0, sizeof(im));
-    im.tap_off = -1;
-    im.in = it.in;
-    im.out = it.out;
-    im.in_pitch = it.in_pitch;
-    im.out_pitch = it.out_pitch;
-    im.in_h = it.out_h + it.k - 1;
-    im.in_w = it.out_w + it.k - 1;
-    im.out_h = it.out_h;
-    im.out_w = it.out_w;
-    im.k = it.k;
-    const int cls = size_class(it.out_h, it.out_w);
-    int bx = 32, ty = 2;
-    if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k], it.k)) {
-      bx = tiles->block_x[cls][it.k];
-      ty = tiles->tile_y[cls][it.k];
-    }
-    im.bx = bx;
-    im.ty = ty;
-    const bool aligned = (uintptr_t)it.in % 16 == 0 && it.in_pitch % 4 == 0 &&
-                         (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
-    im.vw = aligned ? 4 : 1;
-    im.tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
-    im.tiles_y = (it.out_h + batch_item_rows(it.k, bx, ty) - 1) / batch_item_rows(it.k, bx, ty);
+    rc = batch_image_from_item(it, tiles, &im);
+    if (rc != CT_OK) return rc;
     im.first_item = first;
     first += (long long)im.tiles_x * im.tiles_y;
     // taps: k rows padded to round_up(k, 4) floats (the padding is never used
@@ -828,11 +934,12 @@ extern "C" int ct_batch_noalloc_status(unsigned* bits, int clear, void* stream) 
 // ---------------------------------------------------------------------------
 namespace convtune {
 
-int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, BatchImage* im,
-                          size_t* smem) {
+int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, BatchImage* im) {
   if (!it.filt || it.k < 1 || it.k > kMaxK || (it.k & 1) == 0) return CT_EINVAL;
   if (it.out_h <= 0 || it.out_w <= 0 || !it.in || !it.out) return CT_EINVAL;
   if (it.in_pitch < (long)it.out_w + it.k - 1 || it.out_pitch < it.out_w) return CT_EINVAL;
+  if ((long long)it.out_w + it.k > (1LL << 30) || (long long)it.out_h + it.k > (1LL << 30))
+    return CT_EINVAL;
   memset(im, 0, sizeof(*im));
   im->tap_off = -1;
   im->in = it.in;
@@ -845,19 +952,38 @@ int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, 
   im->out_w = it.out_w;
   im->k = it.k;
   const int cls = size_class(it.out_h, it.out_w);
+  const int threads = class_threads(tiles, it.k);
   int bx = 32, ty = 2;
-  if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k], it.k)) {
+  if (tiles && valid_tile(tiles->block_x[cls][it.k], tiles->tile_y[cls][it.k], it.k, threads)) {
     bx = tiles->block_x[cls][it.k];
     ty = tiles->tile_y[cls][it.k];
   }
   im->bx = bx;
   im->ty = ty;
+  im->threads = threads;
+  im->claim = class_claim(tiles, it.k);
   const bool aligned = (uintptr_t)it.in % 16 == 0 && it.in_pitch % 4 == 0 &&
                        (uintptr_t)it.out % 16 == 0 && it.out_pitch % 4 == 0;
   im->vw = aligned ? 4 : 1;
   im->tiles_x = (it.out_w + bx * kBatchTileX - 1) / (bx * kBatchTileX);
-  im->tiles_y = (it.out_h + batch_item_rows(it.k, bx, ty) - 1) / batch_item_rows(it.k, bx, ty);
-  *smem = std::max(*smem, batch_smem_bytes(it.k, bx, ty));
+  const int rows = batch_item_rows(it.k, bx, ty, threads);
+  im->tiles_y = (it.out_h + rows - 1) / rows;
+  im->g = batch_stage_geom(it.k, bx, ty, threads);
+  // TMA staging wants a 16-byte aligned input and row stride; the box
+  // (<= 144 x 144 floats here) is within the 256-element limit
+  const bool in_aligned = (uintptr_t)it.in % 16 == 0 && it.in_pitch % 4 == 0;
+  auto enc = in_aligned ? tensor_map_encoder() : nullptr;
+  if (enc) {
+    const cuuint64_t dims[2] = {(cuuint64_t)im->in_w, (cuuint64_t)im->in_h};
+    const cuuint64_t strides[1] = {(cuuint64_t)it.in_pitch * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)im->g.box_w, (cuuint32_t)im->g.tile_h};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&im->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)it.in, dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    im->use_tma = r == CUDA_SUCCESS ? 1 : 0;
+  }
   return CT_OK;
 }
 

@@ -10,11 +10,13 @@
 
 namespace convtune {
 
-// Fill one table entry from a caller's item (device in/out, taps pointer
-// `it.filt` must already point at k rows of round_up(k, 4) device floats);
-// grows *smem to the entry's shared-memory need.
-int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, BatchImage* im,
-                          size_t* smem);
+// Fill one table entry from a caller's item (device in/out; im->filt is left
+// null for the caller to point at k rows of round_up(k, 4) device floats):
+// tile from `tiles` (or the default), staging geometry, and the TMA tensor
+// map of the input when it is 16-byte aligned (else cp.async staging).
+// first_item and tap_off are the caller's / the plan's to set.  Host only;
+// allocates nothing.
+int batch_image_from_item(const ct_batch_item& it, const ct_batch_tiles* tiles, BatchImage* im);
 
 // Launch plan of a host copy of a batch table, which must be ordered by
 // filter-side class (batch_class_of, ascending).  Each class's contiguous run
@@ -31,6 +33,9 @@ struct BatchClassLaunch {
   long long items = 0;        // work items of the run
   long long item_base = 0;    // first_item of its first image
   size_t smem = 0;            // dynamic shared memory per CTA
+  int buf_floats = 0;         // floats of each staging buffer (largest of the run)
+  int threads = 0;            // CTA size (the class's)
+  int claim = 1;              // work items per claim (the class's)
   int grid = 0;               // persistent CTAs
   std::vector<float> taps;    // the run's parameter-block taps (KP-padded rows)
 };

@@ -75,12 +75,29 @@ cudaError_t CT_CAT(launch_k, CT_K)(const ConvLaunch& L, cudaStream_t s) {
   a.smem_pitch = L.smem_pitch;
   a.tile_w = L.tile_w;
   a.tile_h = L.tile_h;
+  a.group_x = L.group_x;
+  a.group_stride = L.group_stride;
+  a.groups = L.groups;
   for (int j = 0; j < K; ++j) memcpy(a.w + j * KP, L.taps + j * K, sizeof(float) * K);
   const dim3 block(L.bx, L.by);
   const dim3 grid((L.out_w + L.bx * L.tx - 1) / (L.bx * L.tx),
                   (L.out_h + L.by * L.ty - 1) / (L.by * L.ty));
   void* args[] = {&a};
-  return cudaLaunchKernel(fn, grid, block, args, L.smem_bytes, s);
+  // programmatic stream serialization: the launch and prologue may overlap
+  // the previous kernel on the stream (the kernel waits before touching
+  // global memory)
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = L.smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace convtune

@@ -47,7 +47,8 @@ struct alignas(128) ConvArgs {  // (the tensor map needs 128-byte alignment)
   int vw;                    // global load width 1, 2 or 4
   int staging;               // kStageDirect / kStageSmem / kStageTma
   int smem_pitch;            // floats per shared-memory tile row
-  int tile_w, tile_h;        // staged tile (floats); tile_w % 4 == 0
+  int tile_w, tile_h;        // staged box (floats); tile_w % 4 == 0
+  int group_x, group_stride, groups;  // boxes of the staged tile (see ConvLaunch)
   // taps: the specialised kernels keep K rows of KP = round_up(K, 4) floats
   // (zero padded; a tap row is whole 16-byte words), the generic kernel
   // fh rows of fw floats
@@ -168,20 +169,43 @@ __device__ __forceinline__ void mbar_init_fence() {
 }
 
 // Leader thread: arm the mbarrier for the tile's bytes and start one 2-D TMA
-// copy of the tile (tile_w <= 256, tile_h <= 256, x % 4 == 0).
+// copy per box of the tile.  A box is at most 256 x 256 floats, so a tile
+// wider than that is staged as several boxes side by side, one per group of
+// group_x threads in x, each with its own K-1 halo columns (x offsets
+// group_x * TX floats apart: multiples of 4, 16-byte aligned).
 template <class Args>
 __device__ __forceinline__ void issue_tile_tma(const Args& a, float* tile, uint64_t* mbar, int gx0,
-                                               int gy0) {
+                                               int gy0, int tx) {
   const unsigned bar = smem_u32(mbar);
-  const unsigned bytes = static_cast<unsigned>(a.tile_w * a.tile_h * 4);
+  const unsigned bytes = static_cast<unsigned>(a.groups * a.tile_w * a.tile_h * 4);
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
                : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(tile)),
-      "l"(reinterpret_cast<uint64_t>(&a.tmap)), "r"(gx0), "r"(gy0), "r"(bar)
-      : "memory");
+  for (int q = 0; q < a.groups; ++q) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(tile + q * a.group_stride)),
+        "l"(reinterpret_cast<uint64_t>(&a.tmap)), "r"(gx0 + q * a.group_x * tx), "r"(gy0),
+        "r"(bar)
+        : "memory");
+  }
 }
+
+// Programmatic dependent launch.  A launch made with programmatic stream
+// serialization may start while the previous kernel on its stream still
+// runs: pdl_launch_dependents() lets the next launch begin once every CTA
+// of this grid has called it (or exited); pdl_wait() blocks until the
+// previous grid has completed and its memory is visible.  Both are no-ops
+// for a launch made without the attribute.  The correlation kernels wait
+// right before their first global-memory access and trigger right after
+// it: the next launch and its prologue (shared-memory taps, barrier set-up)
+// overlap this grid's run, correct whatever the two kernels share, and at
+// most one grid waits ahead (a trigger before the wait let every queued
+// launch of a CUDA graph start at once: their waiting CTAs crowded the SMs,
+// 1024^2 / 7 x 7 graph replay 4.9 -> 13 us per launch).
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 // Bounded wait for completion of the mbarrier phase with the given parity.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
@@ -456,7 +480,9 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K
         mbar_init_fence();
       }
       __syncthreads();
-      if (leader) issue_tile_tma(a, tile, &full, gx0, gy0);
+      pdl_wait();
+      pdl_launch_dependents();
+      if (leader) issue_tile_tma(a, tile, &full, gx0, gy0, TX);
       const bool ok = mbar_wait(&full, 0u);
       // every thread takes the same decision, so no thread is left at a barrier
       if (__syncthreads_or(!ok)) {
@@ -464,13 +490,17 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K
         return;
       }
     } else {
+      pdl_wait();
+      pdl_launch_dependents();
       issue_tile_cp_async(a, tile, gx0, gy0);
       cp_async_wait_all();
       __syncthreads();
     }
     const int x0 = gx0 + threadIdx.x * TX;
     const int y0 = gy0 + threadIdx.y * TY;
-    const float* sbase = tile + (threadIdx.y * TY) * a.smem_pitch + threadIdx.x * TX;
+    const int grp = threadIdx.x / a.group_x;  // (group_x: a power of two)
+    const float* sbase = tile + grp * a.group_stride + (threadIdx.y * TY) * a.smem_pitch +
+                         (threadIdx.x - grp * a.group_x) * TX;
     // The fully unrolled form runs K*K*TX*TY FFMAs straight through; above
     // ~2500 of them (4 x 4 tiles, K >= 13) its code no longer fits the
     // instruction caches and warps stall on instruction fetch, so those
@@ -511,6 +541,8 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K
     }
   } else {
     if constexpr (FILT_SMEM) __syncthreads();
+    pdl_wait();
+    pdl_launch_dependents();
     const int gx0 = blockIdx.x * bx * TX;  // tile origin (input == output coords)
     const int gy0 = blockIdx.y * by * TY;
     const int x0 = gx0 + threadIdx.x * TX;

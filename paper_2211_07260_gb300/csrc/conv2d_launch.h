@@ -35,6 +35,10 @@ struct ConvLaunch {
   int bx, by, tx, ty;
   int staging, filt_smem, vw;
   int smem_pitch, tile_w, tile_h;
+  // staged tile as boxes side by side in shared memory: threads [q*group_x,
+  // (q+1)*group_x) in x read box q, group_stride floats after box q-1 (one
+  // box of the whole tile: group_x = bx, group_stride = 0)
+  int group_x, group_stride, groups;
   size_t smem_bytes;
   const CUtensorMap* tmap; // valid when staging == TMA
 };

@@ -28,4 +28,21 @@ class ClockLock {
   bool locked_ = false;
 };
 
+// Scoped board power limit: set on construction (when mw > 0), the device's
+// default restored in the destructor if it was set.
+class PowerLimit {
+ public:
+  PowerLimit(const ct_platform_ops& ops, int mw);
+  ~PowerLimit();
+  int status() const { return status_; }
+  bool set() const { return set_; }
+  PowerLimit(const PowerLimit&) = delete;
+  PowerLimit& operator=(const PowerLimit&) = delete;
+
+ private:
+  ct_platform_ops ops_;
+  int status_ = 0;
+  bool set_ = false;
+};
+
 }  // namespace convtune

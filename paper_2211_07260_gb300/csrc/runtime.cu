@@ -102,22 +102,6 @@ KernelLauncher launcher_for(int k) {
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::call_once(once, [] {
-    cudaDriverEntryPointQueryResult q;
-    void* p = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 inline bool one_of_124(int v) { return v == 1 || v == 2 || v == 4; }
 
@@ -136,6 +120,22 @@ cudaError_t raise_smem_cap(DeviceState* st, const void* fn) {
 }
 
 }  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
 
 namespace {
 thread_local char g_last_error[256] = "";
@@ -264,20 +264,34 @@ int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::stri
     if (staged) {
       L.tile_w = round_up(c.block_x * c.tile_x + K - 1, 4);
       L.tile_h = c.block_y * c.tile_y + K - 1;
+      L.group_x = c.block_x;
+      L.group_stride = 0;
+      L.groups = 1;
       if (c.staging == CT_STAGE_TMA) {
-        if (L.tile_w > 256 || L.tile_h > 256)
-          return fail(CT_ECONFIG, "TMA box wider or taller than 256 elements");
+        if (L.tile_h > 256) return fail(CT_ECONFIG, "TMA box taller than 256 elements");
         if ((uintptr_t)p.in % 16 != 0 || (p.in_pitch * 4) % 16 != 0)
           return fail(CT_ECONFIG, "TMA needs a 16-byte aligned input and row stride");
+        // a tile wider than one 256-float box: one box per group of
+        // threads in x, each with its own halo (the widest power-of-two
+        // group whose box fits)
+        while (L.tile_w > 256 && L.group_x > 1) {
+          L.group_x /= 2;
+          L.tile_w = round_up(L.group_x * c.tile_x + K - 1, 4);
+        }
+        if (L.tile_w > 256) return fail(CT_ECONFIG, "TMA box wider than 256 elements");
+        L.groups = c.block_x / L.group_x;
         L.smem_pitch = L.tile_w;
+        L.group_stride = L.groups > 1 ? round_up(L.tile_w * L.tile_h, 32) : 0;
+        smem += sizeof(float) * (size_t)(L.groups > 1 ? L.groups * L.group_stride
+                                                       : L.tile_h * L.smem_pitch);
       } else {
         L.smem_pitch = L.tile_w;
         // half-warp rows of 16 lanes reading 4-byte words: put consecutive
         // tile rows 16 banks apart
         if (c.block_x == 16 && c.tile_x == 1)
           while (L.smem_pitch % 32 != 16) L.smem_pitch += 4;
+        smem += sizeof(float) * (size_t)L.tile_h * L.smem_pitch;
       }
-      smem += sizeof(float) * (size_t)L.tile_h * L.smem_pitch;
     }
     L.smem_bytes = smem;
   }

@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <string>
 
@@ -29,6 +30,9 @@ struct ConvPlan {
 // limits), for simulated measurement.
 int plan_conv(const ct_problem& p, const ct_config& c, ConvPlan* plan, std::string* why,
               bool device_checks = true);
+
+// cuTensorMapEncodeTiled from the driver (null if unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 // Launch a resolved plan on a stream.
 int launch_plan(ConvPlan& plan, cudaStream_t s);

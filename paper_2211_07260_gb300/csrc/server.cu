@@ -111,6 +111,8 @@ struct Slot {
   cudaEvent_t ev = nullptr;
   bool busy = false;
   std::vector<Request*> reqs;
+  ct_server_trace_entry trace;  // the batch in flight (timeline)
+  cudaEvent_t tev[4] = {};       // timeline: start, copies in, kernels, copies out
   BatchImage* d_table = nullptr;
   float* d_taps = nullptr;
   unsigned* d_counter = nullptr;
@@ -147,6 +149,9 @@ struct ct_server {
   unsigned long long e0 = 0;
   bool have_energy = false;
   ct_platform_ops ops;
+  // timeline of completed batches (ring of trace_cap entries)
+  std::vector<ct_server_trace_entry> trace;
+  size_t trace_next = 0, trace_count = 0;
 
   void run();
   int dispatch(Slot& sl, std::vector<Request*>& batch);
@@ -156,13 +161,17 @@ struct ct_server {
 int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
   cudaError_t e;
   int rc = CT_OK;
+  const bool timed = sl.tev[0] != nullptr;
+  if (timed && (e = cudaEventRecord(sl.tev[0], sl.s)) != cudaSuccess) return cuda_status(e);
   // inputs in: whole pitched rows in one contiguous copy (the pool's copy of
   // the caller's padding columns is never read)
   for (Request* r : batch) {
     const size_t bytes = sizeof(float) * (size_t)r->in_pitch * (r->out_h + r->k - 1);
     e = cudaMemcpyAsync(pool + r->off, r->in_host, bytes, cudaMemcpyHostToDevice, sl.s);
     if (e != cudaSuccess) return cuda_status(e);
+    sl.trace.bytes_in += (double)bytes;
   }
+  if (timed && (e = cudaEventRecord(sl.tev[1], sl.s)) != cudaSuccess) return cuda_status(e);
   if (opt.plain) {
     for (Request* r : batch) {
       ct_problem p;
@@ -184,12 +193,11 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
       it.out_h = p.out_h;
       it.out_w = p.out_w;
       BatchImage im;
-      size_t smem = 0;
-      rc = batch_image_from_item(it, opt.use_tiles ? &opt.tiles : nullptr, &im, &smem);
+      rc = batch_image_from_item(it, opt.use_tiles ? &opt.tiles : nullptr, &im);
       if (rc != CT_OK) return rc;
       ct_config c;
       c.block_x = im.bx;
-      c.block_y = kBatchThreads / im.bx;
+      c.block_y = im.threads / im.bx;
       c.tile_x = kBatchTileX;
       c.tile_y = std::min(im.ty, 4);  // (the single-image kernel's tiles are at most 4 high)
       c.staging = CT_STAGE_SMEM;
@@ -203,7 +211,7 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
     std::stable_sort(batch.begin(), batch.end(), [](const Request* x, const Request* y) {
       return batch_class_of(x->k) < batch_class_of(y->k);
     });
-    size_t smem = 16;
+    const double t_plan0 = now_s();
     long long first = 0;
     for (size_t q = 0; q < batch.size(); ++q) {
       Request* r = batch[q];
@@ -217,7 +225,7 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
       it.out_h = r->out_h;
       it.out_w = r->out_w;
       BatchImage& im = sl.h_table[q];
-      rc = batch_image_from_item(it, opt.use_tiles ? &opt.tiles : nullptr, &im, &smem);
+      rc = batch_image_from_item(it, opt.use_tiles ? &opt.tiles : nullptr, &im);
       if (rc != CT_OK) return rc;
       const int kp = (r->k + 3) / 4 * 4;
       float* ht = sl.h_taps + q * kTapFloats;
@@ -234,6 +242,7 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
     for (size_t q = 0; q < n; ++q) host_taps[q] = batch[q]->taps;
     BatchPlan plan;
     if ((rc = plan_batch(sl.h_table, (int)n, host_taps.data(), &plan)) != CT_OK) return rc;
+    sl.trace.plan_s = now_s() - t_plan0;
     if ((e = cudaMemcpyAsync(sl.d_taps, sl.h_taps, sizeof(float) * kTapFloats * n,
                              cudaMemcpyHostToDevice, sl.s)) != cudaSuccess)
       return cuda_status(e);
@@ -246,9 +255,11 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
     if ((rc = enqueue_batch_plan(plan, sl.d_table, sl.d_counter, status, sl.s)) != CT_OK)
       return rc;
   }
+  if (timed && (e = cudaEventRecord(sl.tev[2], sl.s)) != cudaSuccess) return cuda_status(e);
   // outputs back: only the out_w computed columns of each row (the caller's
   // padding columns are left untouched)
   for (Request* r : batch) {
+    sl.trace.bytes_out += sizeof(float) * (double)r->out_w * r->out_h;
     const size_t pitch = sizeof(float) * (size_t)r->out_pitch;
     if (r->out_pitch == r->out_w)  // no padding columns: one contiguous copy
       e = cudaMemcpyAsync(r->out_host, pool + r->off + r->in_bytes, pitch * r->out_h,
@@ -259,6 +270,7 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
                             sl.s);
     if (e != cudaSuccess) return cuda_status(e);
   }
+  if (timed && (e = cudaEventRecord(sl.tev[3], sl.s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaEventRecord(sl.ev, sl.s)) != cudaSuccess) return cuda_status(e);
   sl.busy = true;
   sl.reqs = batch;
@@ -267,7 +279,15 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
 
 void ct_server::run() {
   cudaSetDevice(device);
+  double t_iter = now_s(), max_gap = 0;
+  int n_queued = 0;
   for (;;) {
+    {
+      // pauses of this thread between iterations (timeline)
+      const double t = now_s();
+      max_gap = std::max(max_gap, t - t_iter);
+      t_iter = t;
+    }
     bool idle = true;
     std::vector<Request*> finished;
     // retire finished batches
@@ -288,6 +308,23 @@ void ct_server::run() {
         flop += 2.0 * r->k * r->k * (double)r->out_h * r->out_w;
         t_last = t;
       }
+      if (!trace.empty()) {
+        sl.trace.t_done = t;
+        if (sl.tev[0] && q == cudaSuccess) {
+          float ms[3] = {0, 0, 0};
+          for (int k = 0; k < 3; ++k)
+            if (cudaEventElapsedTime(&ms[k], sl.tev[k], sl.tev[k + 1]) != cudaSuccess) {
+              cudaGetLastError();
+              ms[k] = NAN;
+            }
+          sl.trace.h2d_ms = ms[0];
+          sl.trace.kernels_ms = ms[1];
+          sl.trace.d2h_ms = ms[2];
+        }
+        trace[trace_next] = sl.trace;
+        trace_next = (trace_next + 1) % trace.size();
+        trace_count = std::min(trace_count + 1, trace.size());
+      }
       sl.busy = false;
       sl.reqs.clear();
       cv.notify_all();
@@ -302,6 +339,7 @@ void ct_server::run() {
     {
       std::lock_guard<std::mutex> lk(mu);
       if (stop && queued.empty() && admitted.empty() && !any_busy) break;
+      n_queued = (int)queued.size();
       // admission: arrival order, while the pool has room
       while (!queued.empty()) {
         Request* r = queued.front();
@@ -322,7 +360,18 @@ void ct_server::run() {
     }
     if (!batch.empty()) {
       idle = false;
+      ct_server_trace_entry& te = free_slot->trace;
+      memset(&te, 0, sizeof(te));
+      te.t_dispatch = now_s();
+      te.oldest_wait_s = te.t_dispatch - batch.front()->t_submit;
+      te.loop_gap_s = max_gap;
+      te.n_requests = (int)batch.size();
+      te.slot = (int)(free_slot - slots.data());
+      te.queued = n_queued;
+      for (const Slot& o : slots) te.busy_slots += o.busy ? 1 : 0;
+      max_gap = 0;
       const int rc = dispatch(*free_slot, batch);
+      te.dispatch_s = now_s() - te.t_dispatch;
       std::lock_guard<std::mutex> lk(mu);
       ++batches;
       batched_reqs += (long long)batch.size();
@@ -352,6 +401,8 @@ ct_server::~ct_server() {
       cudaStreamDestroy(sl.s);
     }
     if (sl.ev) cudaEventDestroy(sl.ev);
+    for (cudaEvent_t te : sl.tev)
+      if (te) cudaEventDestroy(te);
     if (sl.h_table) cudaFreeHost(sl.h_table);
     if (sl.h_taps) cudaFreeHost(sl.h_taps);
   }
@@ -367,7 +418,8 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
   if (!opt || !out) return CT_EINVAL;
   *out = nullptr;
   if (opt->n_streams < 1 || opt->n_streams > 64 || opt->max_batch < 1 ||
-      opt->max_batch > 4096 || opt->pool_bytes <= 0 || !(opt->max_wait_s >= 0))
+      opt->max_batch > 4096 || opt->pool_bytes <= 0 || !(opt->max_wait_s >= 0) ||
+      opt->trace_cap < 0 || opt->trace_cap > (1 << 20))
     return CT_EINVAL;
   ct_server* sv = new (std::nothrow) ct_server();
   if (!sv) return CT_ENOMEM;
@@ -406,6 +458,12 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
     sl.d_counter = reinterpret_cast<unsigned*>(base);  // one work counter per launch
     sl.d_table = reinterpret_cast<BatchImage*>(base + kBatchCounterBytes);
     sl.d_taps = reinterpret_cast<float*>(base + kBatchCounterBytes + per_slot_table);
+    if (opt->trace_cap > 0)
+      for (cudaEvent_t& te : sl.tev)
+        if ((e = cudaEventCreate(&te)) != cudaSuccess) {
+          delete sv;
+          return cuda_status(e);
+        }
     if ((e = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMallocHost(&sl.h_table, per_slot_table)) != cudaSuccess ||
@@ -431,13 +489,12 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
         it.in = it.out = reinterpret_cast<float*>(sv->pool);
         it.filt = reinterpret_cast<const float*>(sv->pool);
         BatchImage im;
-        size_t smem = 0;
-        if ((rc = batch_image_from_item(it, opt->use_tiles ? &opt->tiles : nullptr, &im,
-                                        &smem)) != CT_OK)
+        if ((rc = batch_image_from_item(it, opt->use_tiles ? &opt->tiles : nullptr, &im)) !=
+            CT_OK)
           break;
         ct_config c;
         c.block_x = im.bx;
-        c.block_y = kBatchThreads / im.bx;
+        c.block_y = im.threads / im.bx;
         c.tile_x = kBatchTileX;
         c.tile_y = std::min(im.ty, 4);
         c.staging = CT_STAGE_SMEM;
@@ -450,6 +507,7 @@ int ct_server_create(const ct_server_options* opt, ct_server** out) {
       return rc;
     }
   }
+  if (opt->trace_cap > 0) sv->trace.resize((size_t)opt->trace_cap);
   sv->ops = platform_ops();
   sv->t0 = now_s();
   sv->have_energy = sv->ops.energy_mj && sv->ops.energy_mj(sv->ops.ctx, &sv->e0) == CT_OK;
@@ -563,6 +621,18 @@ int ct_server_stats_get(ct_server* sv, int reset, ct_server_stats* out) {
     sv->t0 = t;
     sv->t_last = t;
   }
+  return CT_OK;
+}
+
+int ct_server_trace_get(ct_server* sv, ct_server_trace_entry* out, int cap, int* n) {
+  if (!sv || !n || cap < 0) return CT_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->trace.empty()) return CT_ENOTSUP;
+  *n = (int)sv->trace_count;
+  if ((int)sv->trace_count > cap || (!out && sv->trace_count > 0)) return CT_ENOMEM;
+  const size_t m = sv->trace.size();
+  const size_t first = (sv->trace_next + m - sv->trace_count) % m;
+  for (size_t i = 0; i < sv->trace_count; ++i) out[i] = sv->trace[(first + i) % m];
   return CT_OK;
 }
 

@@ -61,13 +61,15 @@ std::string device_tag(bool simulated) {
 }
 
 std::string point_key(const std::string& dev, const ct_problem& p, const ct_config& c, int clock,
-                      const ct_measure_options& m) {
+                      int limit_mw, const ct_measure_options& m) {
   char buf[512];
   snprintf(buf, sizeof(buf), "%s|%dx%d|k%dx%d|pitch%ld,%ld|cfg%d,%d,%d,%d,%d,%d,%d|clk%d|w%.4g|t%d",
            dev.c_str(), p.out_h, p.out_w, p.fh, p.fw, p.in_pitch, p.out_pitch, c.block_x,
            c.block_y, c.tile_x, c.tile_y, c.staging, c.filter_mem, c.vec_width, clock, m.window_s,
            m.time_only);
-  return buf;
+  std::string k = buf;
+  if (limit_mw > 0) k += "|pl" + std::to_string(limit_mw);  // (clock keys stay as they were)
+  return k;
 }
 
 // ---- JSON-lines cache (flat objects written and read by this file) -------
@@ -95,6 +97,7 @@ std::string record_json(const std::string& key, const ct_record& r) {
   put_num(&s, "wall_s", r.wall_s);
   put_num(&s, "n_launches", r.n_launches);
   put_num(&s, "flags", r.flags);
+  put_num(&s, "power_limit_w", r.power_limit_w);
   return s + "}\n";
 }
 
@@ -148,6 +151,7 @@ int load_cache(const char* path, std::map<std::string, ct_record>* out) {
     num("n_launches", &nl);
     num("flags", &fl);
     if (!ok) continue;
+    if (!get_num(line, "power_limit_w", &r.power_limit_w)) r.power_limit_w = 0;
     r.clock_mhz_req = (int)clk;
     r.n_launches = (int)nl;
     r.flags = (int)fl;
@@ -198,9 +202,16 @@ int select_best(const ct_record* recs, int n, int objective, const int* clocks, 
   return best;
 }
 
-int tune_impl(const ct_problem& p, const ct_config* space, int n_space, const int* clocks,
-              int n_clocks, const ct_tune_options& opt, cudaStream_t stream, ct_record* records,
-              int cap, int* n_records, int* best_index) {
+namespace {
+
+// The exhaustive sweep over configurations x one device setting: SM clocks
+// (power_axis = false; 0 = default clocks) or board power limits in mW
+// (power_axis = true), setting-major so each setting is applied once and
+// undone before the next.
+int tune_axis(const ct_problem& p, const ct_config* space, int n_space, bool power_axis,
+              const int* settings, int n_settings, const ct_tune_options& opt,
+              cudaStream_t stream, ct_record* records, int cap, int* n_records,
+              int* best_index) {
   std::vector<ct_config> builtin;
   if (!space) {
     fill_space(CT_SPACE_BASIC, &builtin);
@@ -209,7 +220,7 @@ int tune_impl(const ct_problem& p, const ct_config* space, int n_space, const in
   }
   if (n_space <= 0) return CT_EINVAL;
   std::vector<int> clk;
-  if (clocks && n_clocks > 0) clk.assign(clocks, clocks + n_clocks);
+  if (settings && n_settings > 0) clk.assign(settings, settings + n_settings);
   else clk.push_back(0);
   const long long needed = (long long)n_space * (long long)clk.size();
   *n_records = (int)needed;
@@ -232,31 +243,39 @@ int tune_impl(const ct_problem& p, const ct_config* space, int n_space, const in
   int rc = CT_OK;
   bool default_clock_fallback = false;
   for (size_t ci = 0; ci < clk.size() && rc == CT_OK; ++ci) {
-    int clock = clk[ci];
+    const int setting = clk[ci];
+    const int clock = power_axis ? 0 : setting;
+    const int limit = power_axis ? setting : 0;
     ClockLock lock(ops, default_clock_fallback ? 0 : clock);
-    if (clock > 0 && !lock.locked()) {
+    PowerLimit plim(ops, default_clock_fallback ? 0 : limit);
+    const bool applied = power_axis ? plim.set() : lock.locked();
+    if (setting > 0 && !applied) {
       if (!opt.fallback_default_clocks) {
-        rc = lock.status() == CT_OK ? CT_EPERM : lock.status();
+        const int st = power_axis ? plim.status() : lock.status();
+        rc = st == CT_OK ? CT_EPERM : st;
         break;
       }
       default_clock_fallback = true;
     }
-    if (lock.locked() && opt.settle_s > 0)
+    if (applied && opt.settle_s > 0)
       std::this_thread::sleep_for(std::chrono::duration<double>(opt.settle_s));
     for (int i = 0; i < n_space; ++i) {
       ct_record& r = records[written];
       memset(&r, 0, sizeof(r));
       r.cfg = space[i];
       r.clock_mhz_req = clock;
+      r.power_limit_w = limit / 1000.0;
       if (default_clock_fallback) r.flags |= CT_REC_DEFAULT_CLOCKS;
       const int rec_clock = default_clock_fallback ? 0 : clock;
-      const std::string key = point_key(dev, p, space[i], rec_clock, mopt);
+      const int rec_limit = default_clock_fallback ? 0 : limit;
+      const std::string key = point_key(dev, p, space[i], rec_clock, rec_limit, mopt);
       auto hit = cache.find(key);
       if (hit != cache.end()) {
         const int keep = r.flags;
         r = hit->second;
         r.cfg = space[i];
         r.clock_mhz_req = clock;
+        r.power_limit_w = limit / 1000.0;
         r.flags |= CT_REC_CACHED | keep;
         ++written;
         continue;
@@ -299,6 +318,7 @@ int tune_impl(const ct_problem& p, const ct_config* space, int n_space, const in
       }
       r = m;
       r.clock_mhz_req = clock;
+      r.power_limit_w = limit / 1000.0;
       if (cf) {
         const std::string line = record_json(key, r);
         fputs(line.c_str(), cf);
@@ -313,6 +333,22 @@ int tune_impl(const ct_problem& p, const ct_config* space, int n_space, const in
   if (rc == CT_OK) *best_index = select_best(records, written, opt.objective, nullptr, 0);
   (void)flop;
   return rc;
+}
+
+}  // namespace
+
+int tune_impl(const ct_problem& p, const ct_config* space, int n_space, const int* clocks,
+              int n_clocks, const ct_tune_options& opt, cudaStream_t stream, ct_record* records,
+              int cap, int* n_records, int* best_index) {
+  return tune_axis(p, space, n_space, false, clocks, n_clocks, opt, stream, records, cap,
+                   n_records, best_index);
+}
+
+int tune_power_impl(const ct_problem& p, const ct_config* space, int n_space, const int* limits_mw,
+                    int n_limits, const ct_tune_options& opt, cudaStream_t stream,
+                    ct_record* records, int cap, int* n_records, int* best_index) {
+  return tune_axis(p, space, n_space, true, limits_mw, n_limits, opt, stream, records, cap,
+                   n_records, best_index);
 }
 
 }  // namespace convtune
@@ -336,6 +372,20 @@ int ct_select_best(const ct_record* recs, int n, int objective, const int* clock
   if (!recs || n < 0 || !best_index || (n_clocks > 0 && !clocks)) return CT_EINVAL;
   *best_index = select_best(recs, n, objective, clocks, n_clocks);
   return CT_OK;
+}
+
+int ct_tune_power_limits(const ct_problem* p, const ct_config* space, int n_space,
+                         const int* limits_mw, int n_limits, const ct_tune_options* opt,
+                         void* stream, ct_record* records, int cap, int* n_records,
+                         int* best_index) {
+  if (!p || !opt || !n_records || !best_index) return CT_EINVAL;
+  if (opt->objective < CT_OBJ_TIME || opt->objective > CT_OBJ_GFLOPS_PER_W) return CT_EINVAL;
+  if (n_limits < 0 || (n_limits > 0 && !limits_mw)) return CT_EINVAL;
+  for (int i = 0; i < n_limits; ++i)
+    if (limits_mw[i] <= 0) return CT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return tune_power_impl(*p, space, n_space, limits_mw, n_limits, *opt, (cudaStream_t)stream,
+                         records, cap, n_records, best_index);
 }
 
 int ct_tune(const ct_problem* p, const ct_config* space, int n_space, const int* clocks_mhz,

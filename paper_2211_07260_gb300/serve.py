@@ -43,18 +43,42 @@ def idle_power(seconds=1.0):
     return float(np.median(samples))
 
 
+def trace_summary(trace, top=5):
+    """Where the slowest batches' time went: waiting before the worker took
+    them, enqueueing, device and copies, and pauses of the worker thread."""
+    rows = []
+    for e in trace:
+        dev = e["t_done"] - e["t_dispatch"] - e["dispatch_s"]
+        rows.append(dict(latency_ms=(e["oldest_wait_s"] + e["t_done"] - e["t_dispatch"]) * 1e3,
+                         wait_ms=e["oldest_wait_s"] * 1e3, enqueue_ms=e["dispatch_s"] * 1e3,
+                         plan_ms=e["plan_s"] * 1e3, device_and_copies_ms=dev * 1e3,
+                         worker_pause_ms=e["loop_gap_s"] * 1e3, requests=e["n_requests"],
+                         queued=e["queued"], busy_slots=e["busy_slots"],
+                         h2d_ms=e["h2d_ms"], kernels_ms=e["kernels_ms"], d2h_ms=e["d2h_ms"],
+                         h2d_gbs=e["bytes_in"] / max(e["h2d_ms"], 1e-6) / 1e6,
+                         d2h_gbs=e["bytes_out"] / max(e["d2h_ms"], 1e-6) / 1e6))
+    rows.sort(key=lambda r: -r["latency_ms"])
+    gaps = sorted((e["loop_gap_s"] * 1e3 for e in trace), reverse=True)
+    return dict(batches=len(trace), slowest=rows[:top],
+                worker_pause_ms_max=gaps[0] if gaps else None,
+                worker_pauses_over_5ms=sum(g > 5.0 for g in gaps),
+                enqueue_ms_max=max((r["enqueue_ms"] for r in rows), default=None))
+
+
 def serve_rate(payloads, rate, seconds, max_requests, seed=3, plain=False, tiles=None,
-               n_streams=4, max_batch=64, max_wait_s=200e-6, pool_bytes=16 << 30, p_idle=None):
+               n_streams=4, max_batch=64, max_wait_s=200e-6, pool_bytes=16 << 30, p_idle=None,
+               trace_cap=0):
     n = int(min(max_requests, max(1, rate * seconds)))
     arrivals = synth.poisson_arrivals(rate, n, seed)
     with api.Server(n_streams=n_streams, max_batch=max_batch, pool_bytes=pool_bytes,
-                    max_wait_s=max_wait_s, plain=plain, tiles=tiles) as sv:
+                    max_wait_s=max_wait_s, plain=plain, tiles=tiles, trace_cap=trace_cap) as sv:
         # warm-up (kernels loaded, pool touched), then a fresh statistics span
         for i in range(min(8, len(payloads))):
             p, inp, out = payloads[i]
             sv.submit(inp, p.filt, out, p.out_h, p.out_w)
         sv.drain()
         sv.stats(reset=True)
+        t_warm = max((e["t_dispatch"] for e in sv.trace()), default=0.0) if trace_cap else 0.0
         t0 = time.perf_counter()
         for i in range(n):
             target = t0 + arrivals[i]
@@ -69,6 +93,7 @@ def serve_rate(payloads, rate, seconds, max_requests, seed=3, plain=False, tiles
         submit_lag = time.perf_counter() - (t0 + arrivals[-1])
         sv.drain(timeout_s=600.0)
         st = sv.stats()
+        trace = sv.trace() if trace_cap else None
     res = dict(rate_hz=rate, mode="plain" if plain else "batched", requests=st["completed"],
                p50_ms=st["p50_s"] * 1e3, p99_ms=st["p99_s"] * 1e3, max_ms=st["max_s"] * 1e3,
                req_per_s=st["completed"] / st["wall_s"], gflops=st["flop"] / st["wall_s"] / 1e9,
@@ -80,6 +105,9 @@ def serve_rate(payloads, rate, seconds, max_requests, seed=3, plain=False, tiles
         above = st["energy_j"] - p_idle * st["wall_s"]
         res["p_idle_w"] = p_idle
         res["j_per_req_above_idle"] = above / max(1, st["completed"])
+    if trace is not None:
+        # only the batches of the measured span (after the warm-up's last one)
+        res["trace"] = trace_summary([e for e in trace if e["t_dispatch"] > t_warm])
     return res
 
 
@@ -92,18 +120,20 @@ def main():
     ap.add_argument("--modes", default="batched,plain")
     ap.add_argument("--tiles", default=None, help="JSON file of per-bucket tiles")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--trace", type=int, default=0,
+                    help="keep a timeline of the last N batches and report the slowest")
     a = ap.parse_args()
     tiles = None
     if a.tiles:
         raw = json.load(open(a.tiles))
-        tiles = {tuple(int(x) for x in k.split(",")): tuple(v) for k, v in raw.items()}
+        tiles = api.tiles_from_json(raw)
     payloads = make_payloads(a.payloads)
     p_idle = idle_power()
     rows = []
     for rate in [float(r) for r in a.rates.split(",")]:
         for mode in a.modes.split(","):
             r = serve_rate(payloads, rate, a.seconds, a.max_requests, plain=(mode == "plain"),
-                           tiles=tiles, p_idle=p_idle)
+                           tiles=tiles, p_idle=p_idle, trace_cap=a.trace)
             print(json.dumps(r), flush=True)
             rows.append(r)
     if a.out:

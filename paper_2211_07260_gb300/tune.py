@@ -95,13 +95,12 @@ def tune_batched(objective="energy", window=0.3, out=None, n=256, seed=2, log=pr
     t0 = time.time()
     tiles, recs = api.batch_tune(ents, objective, api.measure_options(window_s=window,
                                                                       warmup_s=0.1))
-    log(json.dumps(dict(batched_tiles={f"{c},{k}": v for (c, k), v in tiles.items()},
-                        points=len(recs), wall_s=time.time() - t0)))
+    log(json.dumps(dict(batched_tiles=api.tiles_to_json(tiles), points=len(recs),
+                        wall_s=time.time() - t0)))
     if out:
         table = json.load(open(out)) if os.path.exists(out) else {"devices": {}}
         name = api.device_info()["name"]
-        table.setdefault("batched_tiles", {})[name] = {f"{c},{k}": list(v)
-                                                       for (c, k), v in tiles.items()}
+        table.setdefault("batched_tiles", {})[name] = api.tiles_to_json(tiles)
         with open(out, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
             f.write("\n")

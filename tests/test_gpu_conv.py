@@ -32,11 +32,14 @@ def test_every_config_matches_oracle_and_each_other_bitwise(k):
     d_in, full, d_out = to_device(prob, out_pitch=144, guard_rows=2)
     first = None
     n_run = n_pruned = 0
+    ok_cfgs, pruned = set(), {}
     for cfg in full_space():
         rc, why = api.conv2d_check(d_in, prob.filt, d_out, prob.out_h, prob.out_w, cfg)
         if rc == api.CT_ECONFIG:
             n_pruned += 1
+            pruned[cfg.as_tuple()] = why
             continue
+        ok_cfgs.add(cfg.as_tuple())
         assert rc == api.CT_OK, (cfg, why)
         full.fill_(-7.0)
         run(prob, cfg, d_in, d_out)
@@ -53,9 +56,15 @@ def test_every_config_matches_oracle_and_each_other_bitwise(k):
             assert np.array_equal(out.view(np.uint32), first.view(np.uint32)), cfg
         n_run += 1
     assert api.status_read(clear=True) == 0
+    # TMA points pruned although the same point with cp.async staging runs
+    tma_only = {c: w for c, w in pruned.items()
+                if c[4] == api.STAGE_TMA and c[:4] + (api.STAGE_SMEM,) + c[5:] in ok_cfgs}
+    n_tma_only_pruned = len(tma_only)
+    # wide TMA tiles are staged as several boxes: only blocks the registers or
+    # shared memory cannot hold are pruned, never a TMA point whose direct or
+    # cp.async twin runs
     assert n_run > 1000
-    # only TMA tiles wider than 256 floats and register-limited blocks are pruned
-    assert n_pruned < 900
+    assert n_tma_only_pruned == 0, tma_only
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 37), (29, 1), (2, 2), (17, 17), (64, 64),

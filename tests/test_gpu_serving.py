@@ -82,3 +82,28 @@ def test_poisson_driver_reports_latency_and_energy():
         assert r["requests"] == 1000
         assert 0 < r["p50_ms"] <= r["p99_ms"]
         assert r["energy_j"] > 0 and r["j_per_req"] > 0
+
+
+def test_timeline_accounts_for_every_batch():
+    mix = _payloads(60, seed=25)
+    with api.Server(n_streams=2, max_batch=8, pool_bytes=1 << 30, trace_cap=1000) as sv:
+        for p, inp, out in mix:
+            sv.submit(inp, p.filt, out, p.out_h, p.out_w)
+        sv.drain()
+        st = sv.stats()
+        tr = sv.trace()
+    assert len(tr) == st["batches"] and sum(e["n_requests"] for e in tr) == len(mix)
+    for e in tr:
+        assert e["t_done"] >= e["t_dispatch"] + e["dispatch_s"] >= e["t_dispatch"]
+        assert 0.0 <= e["plan_s"] <= e["dispatch_s"] and e["oldest_wait_s"] >= 0.0
+        assert 0 <= e["slot"] < 2 and 0 <= e["busy_slots"] <= 1 and 1 <= e["n_requests"] <= 8
+        # device-side split of the batch: copies in, kernels, copies out
+        assert e["h2d_ms"] > 0 and e["kernels_ms"] > 0 and e["d2h_ms"] > 0
+        assert e["h2d_ms"] + e["kernels_ms"] + e["d2h_ms"] <= (e["t_done"] - e["t_dispatch"]) * 1e3
+        assert e["bytes_in"] > 0 and e["bytes_out"] > 0
+    with api.Server(n_streams=1, max_batch=4, pool_bytes=1 << 28) as sv:  # no timeline kept
+        with pytest.raises(api.ConvTuneError) as e:
+            sv.trace()
+        assert e.value.status == api.CT_ENOTSUP
+    for p, inp, out in mix:
+        assert max_rel_err(out[:, :p.out_w], oracle_ref(p)) <= MAX_REL
