@@ -153,15 +153,18 @@ __global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int kFilt = batch_filt_floats(batch_class_max_k(CLS));
   float* const sfilt = reinterpret_cast<float*>(smem_raw);
-  float* const bufs = sfilt + kFilt;  // two staging buffers of a.buf_floats
-  __shared__ __align__(8) uint64_t mbar[2];
+  float* const bufs = sfilt + kFilt;  // nb staging buffers of a.buf_floats
+  constexpr int nb = batch_class_stages(CLS);
+  constexpr int nslot = nb + 1;
+  __shared__ __align__(8) uint64_t mbar[kBatchMaxStages];
   // Work-item ring: item i's image entry (copied from the table), image index
-  // and tile sit in slot i % 3.  Warp 0 fills slot (i+2) % 3 and lane 0
-  // starts item i+1's input copy into staging buffer (i+1) % 2 at the start
-  // of item i; the CTA then computes item i.  Claims run a chunk ahead.
-  __shared__ __align__(128) BatchImage s_desc[3];
-  __shared__ long long s_tile[3];
-  __shared__ int s_img[3];
+  // and tile sit in slot i % (nb + 1).  At the start of item i lane 0 starts
+  // the input copy of item i + nb - 1 into staging buffer (i + nb - 1) % nb
+  // (the one item i - 1 used) and warp 0 describes item i + nb in the slot
+  // item i - 1 held; the CTA then computes item i.  Claims run a chunk ahead.
+  __shared__ __align__(128) BatchImage s_desc[kBatchMaxStages + 1];
+  __shared__ long long s_tile[kBatchMaxStages + 1];
+  __shared__ int s_img[kBatchMaxStages + 1];
   __shared__ long long s_first[kBatchFirstCache];
   __shared__ BatchClaimState s_claim;
   const int tid = threadIdx.x;
@@ -170,8 +173,7 @@ __global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
   if (a.n_images <= kBatchFirstCache)
     for (int q = tid; q < a.n_images; q += blockDim.x) s_first[q] = a.images[q].first_item;
   if (tid == 0) {
-    mbar_init(&mbar[0]);
-    mbar_init(&mbar[1]);
+    for (int q = 0; q < nb; ++q) mbar_init(&mbar[q]);
     mbar_init_fence();
     s_claim.cur = s_claim.end = 0;
     s_claim.first = s_claim.last = -1;
@@ -180,38 +182,42 @@ __global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
   }
   __syncthreads();
   if (warp0) {
-    // prologue: items 0 and 1 described, item 0's copy started
-    for (int q = 0; q < 2; ++q) {
-      unsigned w = 0;
-      if (tid == 0) w = batch_next_item(a, &s_claim, &next_chunk);
+    // prologue: items 0 .. nb-1 described, the copies of items 0 .. nb-2
+    // started
+    for (int q = 0; q < nb; ++q) {
+      unsigned w = (unsigned)a.n_items;
+      if (tid == 0 && (q == 0 || s_img[q - 1] != -1)) w = batch_next_item(a, &s_claim, &next_chunk);
       batch_fill_slot(a, w, q, q - 1, &s_claim, s_first, s_desc, s_tile, s_img);
     }
-    if (tid == 0 && s_img[0] >= 0 && s_desc[0].use_tma)
-      batch_issue_tma(&s_desc[0], a.images + s_img[0], (int)s_tile[0], bufs, &mbar[0]);
+    if (tid == 0)
+      for (int q = 0; q + 1 < nb; ++q)
+        if (s_img[q] >= 0 && s_desc[q].use_tma)
+          batch_issue_tma(&s_desc[q], a.images + s_img[q], (int)s_tile[q], bufs + q * a.buf_floats,
+                          &mbar[q]);
   }
   __syncthreads();
   unsigned phase = 0;  // bit b: parity of mbar[b]'s next phase
   for (int i = 0;; ++i) {
-    const int c3 = i % 3, n3 = (i + 1) % 3, f3 = (i + 2) % 3;
-    const int b = i & 1;
-    const int img = s_img[c3];
+    const int cs = i % nslot;               // item i's slot
+    const int ls = (i + nb - 1) % nslot;    // the last described item's slot
+    const int fs = (i + nb) % nslot;        // the slot item i - 1 held
+    const int b = i % nb;
+    const int img = s_img[cs];
     if (img == -1) break;
     float* const buf = bufs + b * a.buf_floats;
     if (warp0) {
-      // item i+1's copy (into the buffer item i-1 used: every thread passed
-      // the barrier after computing it), then item i+2 into ring slot f3
-      // (it held item i-1)
-      if (tid == 0 && s_img[n3] >= 0 && s_desc[n3].use_tma)
-        batch_issue_tma(&s_desc[n3], a.images + s_img[n3], (int)s_tile[n3],
-                        bufs + (b ^ 1) * a.buf_floats, &mbar[b ^ 1]);
+      const int lb = (i + nb - 1) % nb;
+      if (tid == 0 && s_img[ls] >= 0 && s_desc[ls].use_tma)
+        batch_issue_tma(&s_desc[ls], a.images + s_img[ls], (int)s_tile[ls],
+                        bufs + lb * a.buf_floats, &mbar[lb]);
       unsigned w = (unsigned)a.n_items;
-      if (tid == 0 && s_img[n3] != -1) w = batch_next_item(a, &s_claim, &next_chunk);
-      batch_fill_slot(a, w, f3, n3, &s_claim, s_first, s_desc, s_tile, s_img);
+      if (tid == 0 && s_img[ls] != -1) w = batch_next_item(a, &s_claim, &next_chunk);
+      batch_fill_slot(a, w, fs, ls, &s_claim, s_first, s_desc, s_tile, s_img);
     }
     bool ok = true;
     if (img >= 0) {
-      const BatchImage& im = s_desc[c3];
-      const int tl = (int)s_tile[c3];  // tiles of one image fit 32 bits
+      const BatchImage& im = s_desc[cs];
+      const int tl = (int)s_tile[cs];  // tiles of one image fit 32 bits
       const bool param_taps = im.tap_off >= 0;  // CTA-uniform, like use_tma
       if (!param_taps) {
         const int kp = (im.k + 3) / 4 * 4;
@@ -229,15 +235,18 @@ __global__ void __launch_bounds__(kBatchThreads, batch_class_min_ctas(CLS))
     } else if (tid == 0) {
       atomicOr(a.status, kStatusBadItem);
     }
-    // the buffer and the ring slots are rewritten only after this point
+    // the buffers and the ring slots are rewritten only after this point
     if (__syncthreads_or(!ok)) {
       // a copy never completed: report it, give the copies still in flight
-      // (this item's, and the next item's if it has one) a bounded wait to
+      // (this item's and those of the next nb - 1 items) a bounded wait to
       // land, and stop this CTA
       if (tid == 0) {
         atomicOr(a.status, kStatusTmaTimeout);
         mbar_wait(&mbar[b], ((phase >> b) & 1u) ^ 1u);
-        if (s_img[n3] >= 0 && s_desc[n3].use_tma) mbar_wait(&mbar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+        for (int d = 1; d < nb; ++d) {
+          const int sl = (i + d) % nslot, bb = (i + d) % nb;
+          if (s_img[sl] >= 0 && s_desc[sl].use_tma) mbar_wait(&mbar[bb], (phase >> bb) & 1u);
+        }
       }
       return;
     }
@@ -259,9 +268,10 @@ constexpr size_t kBatchBranches = 8;  // parallel branches of a captured batch g
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 // Dynamic shared memory of a class launch whose largest staging buffer is
-// buf_floats: the class's shared-memory tap area and two buffers.
-size_t batch_launch_smem(int cls, int buf_floats) {
-  return sizeof(float) * (size_t)(batch_filt_floats(batch_class_max_k(cls)) + 2 * buf_floats);
+// buf_floats: the class's shared-memory tap area and `stages` buffers.
+size_t batch_launch_smem(int cls, int buf_floats, int stages) {
+  return sizeof(float) *
+         (size_t)(batch_filt_floats(batch_class_max_k(cls)) + stages * buf_floats);
 }
 
 bool valid_tile(int bx, int ty, int k, int threads) {
@@ -332,10 +342,11 @@ int plan_batch(BatchImage* table, int n, const float* const* host_taps, BatchPla
     for (int q = L.lo; q < L.hi; ++q)  // one CTA size and claim size per launch
       if (table[q].threads != L.threads || table[q].claim != L.claim) return CT_EINVAL;
     L.buf_floats = buf;
-    L.smem = batch_launch_smem(L.cls, buf);
     cudaFuncAttributes fa;
     cudaError_t e2 = cudaFuncGetAttributes(&fa, batched_kernel_fn(L.cls));
     if (e2 != cudaSuccess) return cuda_status(e2);
+    L.stages = batch_class_stages(L.cls);
+    L.smem = batch_launch_smem(L.cls, buf, L.stages);
     if (L.smem + fa.sharedSizeBytes > (size_t)optin) return CT_ECONFIG;
     int per_sm = 0;
     if ((e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_fn(L.cls),

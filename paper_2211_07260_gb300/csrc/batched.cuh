@@ -31,6 +31,12 @@ constexpr int kBatchThreads = 256;
 // each class alone: sides 1-7 177 -> 165 us with 2, 9-11 and 13-17 fastest
 // with 1).
 __host__ __device__ constexpr int batch_default_claim(int cls) { return cls == 0 ? 2 : 1; }
+// Staging buffers of a class kernel (copies run stages - 1 items ahead).
+// Two for every class: three for sides 1-7 (short items against their
+// copies) measured 148 -> 175 us on GB300, the third buffer of their 8-row
+// 3 x 3 tiles costing a resident CTA.
+constexpr int kBatchMaxStages = 3;
+__host__ __device__ constexpr int batch_class_stages(int /*cls*/) { return 2; }
 __host__ __device__ constexpr bool batch_valid_threads(int t) { return t == 64 || t == 128 || t == 256; }
 constexpr int kBatchTileX = 4;
 // Filter sides up to this one may also take 8-row tiles (their bodies are
@@ -116,7 +122,7 @@ struct BatchArgs {
   long long item_base;       // first_item of images[0]: item w is table item item_base + w
   unsigned* counter;         // work counter, zero at launch
   unsigned* status;          // device status word
-  int buf_floats;            // floats of each of the two staging buffers
+  int buf_floats;            // floats of each staging buffer
   unsigned claim_items;      // consecutive work items each counter increment hands out
   alignas(16) float w[kBatchParamTaps];  // taps of the images with tap_off >= 0
 };

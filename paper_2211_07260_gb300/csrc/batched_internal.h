@@ -36,6 +36,7 @@ struct BatchClassLaunch {
   int buf_floats = 0;         // floats of each staging buffer (largest of the run)
   int threads = 0;            // CTA size (the class's)
   int claim = 1;              // work items per claim (the class's)
+  int stages = 2;             // staging buffers
   int grid = 0;               // persistent CTAs
   std::vector<float> taps;    // the run's parameter-block taps (KP-padded rows)
 };
