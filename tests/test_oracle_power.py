@@ -190,3 +190,36 @@ def test_range_empty_window_falls_back_to_nearest():
 def test_rejects_too_few_samples():
     with pytest.raises(ValueError):
         pm.fit_power_model([1000.0, 1100.0], [100.0, 120.0])
+
+
+@pytest.mark.parametrize("seed", [2, 3, 4])
+def test_noisy_fit_equals_variable_projection_to_1e_9(seed):
+    # An algorithm unrelated to Levenberg-Marquardt: at the oracle's tau the
+    # model is linear in (P_idle, alpha) once beta is fixed, so the least-
+    # squares residual is a function of beta alone (closed-form inner solve);
+    # its minimiser is bracketed on a grid and refined by Brent's method to
+    # the last bits.  The oracle's coefficients must agree to 1e-9 relative.
+    p0, a, b, tau, f = CASES[1]
+    rng = np.random.default_rng(seed)
+    p = curve(f, p0, a, b, tau) + rng.normal(0, 0.5, f.size)
+    m = pm.fit_power_model(f, p, p_max_w=1500.0)
+    fg = f / 1000.0
+    d = np.maximum(0.0, f - m["tau_mhz"]) / 1000.0
+
+    def inner(beta):
+        x = fg * (1.0 + beta * d) ** 2
+        xm, pm_ = x.mean(), p.mean()
+        alpha = float(((x - xm) * (p - pm_)).sum() / ((x - xm) ** 2).sum())
+        p_idle = float(pm_ - alpha * xm)
+        r = p - p_idle - alpha * x
+        return float(r @ r), p_idle, alpha
+
+    grid = np.linspace(0.0, 20.0, 4001)
+    k = int(np.argmin([inner(g)[0] for g in grid]))
+    lo, hi = grid[max(k - 1, 0)], grid[min(k + 1, grid.size - 1)]
+    br = scipy.optimize.minimize_scalar(lambda bb: inner(bb)[0], bounds=(lo, hi),
+                                        method="bounded", options={"xatol": 1e-15})
+    s, p_idle, alpha = inner(br.x)
+    np.testing.assert_allclose([p_idle, alpha, br.x], [m["p_idle_w"], m["alpha"], m["beta"]],
+                               rtol=1e-9)
+    assert m["sse"] == pytest.approx(s, rel=1e-9)
