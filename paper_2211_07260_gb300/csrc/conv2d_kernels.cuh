@@ -13,9 +13,10 @@
 //   staging           DIRECT: each thread reads its rows straight from global
 //                     memory (vector loads through L1), the horizontal halo of
 //                     a row comes from neighbouring lanes by warp shuffles;
-//                     SMEM: the CTA's halo tile is copied to shared memory with
-//                     cp.async; TMA: the same tile arrives by one 2-D
-//                     cp.async.bulk.tensor copy completing on an mbarrier.
+//                     SMEM: the CTA's halo tile is copied to shared memory
+//                     (one bulk copy per row with 16-byte loads, else
+//                     cp.async chunks); TMA: the same tile arrives by 2-D
+//                     cp.async.bulk.tensor copies completing on an mbarrier.
 //                     One output tile per CTA in every mode.
 //   filter memory     CONST: taps are read from the kernel's parameter space
 //                     (constant bank, an immediate FFMA operand once the tap
@@ -221,6 +222,54 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
     if (done) return true;
   }
   return false;
+}
+
+// Shared-memory staging with 16-byte loads (vec_width 4, so the input and its
+// row stride are 16-byte aligned): one bulk copy (cp.async.bulk) per tile
+// row, issued by the first warp and completing on an mbarrier, instead of a
+// 16-byte cp.async per thread and chunk -- a few dozen requests per CTA
+// instead of thousands (1024^2 / 7 x 7: the per-chunk form cost ~1.5 us of
+// every launch).  Rows below the input and the columns past the end of a
+// row's allocation (pitch) are zero-filled in shared memory; a row copy
+// never reads past its row's pitch.  All threads call this; returns false
+// if the bounded wait for the copies gave up.
+template <class Args>
+__device__ __forceinline__ bool stage_tile_bulk_rows(const Args& a, float* tile, uint64_t* mbar,
+                                                     int gx0, int gy0) {
+  const int nthr = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int rows_in = max(0, min(a.tile_h, a.in_h - gy0));
+  const long long avail = a.in_pitch - gx0;  // floats to the end of the row's pitch (> 0)
+  const int cols = (int)(avail < a.tile_w ? avail : a.tile_w);  // a multiple of 4
+  // zero-fill what no copy writes: whole rows below the input, and the
+  // columns past `cols` of the copied rows
+  const int tail = a.tile_w - cols;
+  for (int q = tid; q < rows_in * tail; q += nthr)
+    tile[(q / tail) * a.smem_pitch + cols + q % tail] = 0.0f;
+  for (int q = tid; q < (a.tile_h - rows_in) * a.tile_w; q += nthr)
+    tile[(rows_in + q / a.tile_w) * a.smem_pitch + q % a.tile_w] = 0.0f;
+  if (rows_in > 0) {
+    const int lanes = nthr < 32 ? nthr : 32;  // the first warp (CTAs of 16 threads: half of one)
+    if (tid < lanes) {
+      const unsigned bar = smem_u32(mbar);
+      const unsigned row_bytes = static_cast<unsigned>(cols * 4);
+      if (tid == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                     "r"(row_bytes * static_cast<unsigned>(rows_in))
+                     : "memory");
+      __syncwarp(lanes == 32 ? 0xffffffffu : (1u << lanes) - 1u);
+      for (int r = tid; r < rows_in; r += lanes) {
+        const float* src = a.in + (long long)(gy0 + r) * a.in_pitch + gx0;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(tile + r * a.smem_pitch)),
+            "l"(src), "r"(row_bytes), "r"(bar)
+            : "memory");
+      }
+    }
+    if (!mbar_wait(mbar, 0u)) return false;
+  }
+  return true;
 }
 
 // ----------------------------------------------------------------------------
@@ -484,9 +533,30 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K
       pdl_launch_dependents();
       if (leader) issue_tile_tma(a, tile, &full, gx0, gy0, TX);
       const bool ok = mbar_wait(&full, 0u);
-      // every thread takes the same decision, so no thread is left at a barrier
+      // every thread takes the same decision, so no thread is left at a
+      // barrier; the copy gets one more bounded wait to land before the
+      // CTA leaves
       if (__syncthreads_or(!ok)) {
-        if (leader && a.status) atomicOr(a.status, kStatusTmaTimeout);
+        if (leader) {
+          if (a.status) atomicOr(a.status, kStatusTmaTimeout);
+          mbar_wait(&full, 0u);
+        }
+        return;
+      }
+    } else if (a.vw == 4) {
+      if (leader) {
+        mbar_init(&full);
+        mbar_init_fence();
+      }
+      __syncthreads();
+      pdl_wait();
+      pdl_launch_dependents();
+      const bool ok = stage_tile_bulk_rows(a, tile, &full, gx0, gy0);
+      if (__syncthreads_or(!ok)) {
+        if (leader) {
+          if (a.status) atomicOr(a.status, kStatusTmaTimeout);
+          mbar_wait(&full, 0u);
+        }
         return;
       }
     } else {
