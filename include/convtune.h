@@ -613,11 +613,16 @@ int ct_batch_destroy(ct_batch* b);
 int ct_measure_batch(ct_batch* b, int plain, const ct_measure_options* opt, void* stream,
                      ct_record* out);
 /*
- * Per-bucket tile tuning: for every (size class, filter side) present, the
- * bucket's images are measured together as one batch for block_x in
- * {16, 32, 64, 128} x tile_y in {1, 2, 4} (and 8 for k <= 3) and the
- * objective's best is kept.  records (optional: 16 per bucket with k <= 3,
- * 12 per other bucket) receive the measurements.
+ * Per-bucket tile tuning: for every (size class, filter side) present,
+ * block_x in {16, 32, 64, 128} (at most the class's CTA size) x tile_y in
+ * {1, 2, 4} (and 8 for k <= 3) are measured and the objective's best is
+ * kept.  Each candidate is measured on all the images of the bucket's
+ * filter-side class as one batch, the class's other buckets at their current
+ * tiles (one bucket after another): a class launch's staging buffers and
+ * occupancy follow its largest tile.  `tiles` is read first -- its class CTA
+ * sizes and claim sizes are kept and its valid tiles are the starting point
+ * -- then receives the result.  records (optional: 16 per bucket with
+ * k <= 3, 12 per other bucket at most) receive the measurements.
  */
 int ct_batch_tune(const ct_batch_item* items, int n, int objective,
                   const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,

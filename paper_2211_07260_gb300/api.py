@@ -808,11 +808,13 @@ class Batch:
         self.destroy()
 
 
-def batch_tune(entries, objective="energy", opts=None, stream=None, class_threads=None):
+def batch_tune(entries, objective="energy", opts=None, stream=None, class_threads=None,
+               start: dict | None = None):
     """Per-bucket tiles by the tuner (ct_batch_tune): (tiles dict, records).
-    class_threads: optional CTA size per filter-side class to tune with."""
+    class_threads: optional CTA size per filter-side class to tune with;
+    start: optional tiles dict to start the search from."""
     items, keep = batch_items(entries)
-    t = CtBatchTiles()
+    t = CtBatchTiles.from_dict(start) if start else CtBatchTiles()
     for c, n in enumerate(class_threads or ()):
         t.class_threads[c] = int(n)
     cap = 12 * 2 * 18

@@ -697,24 +697,30 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
                   ct_record* records, int cap, int* n_records) {
   if (!items || n <= 0 || !tiles || !n_records) return CT_EINVAL;
   if (objective < CT_OBJ_TIME || objective > CT_OBJ_GFLOPS_PER_W) return CT_EINVAL;
-  // the caller's class CTA sizes and claim sizes (0: default) are kept and
-  // tuned with
-  int cls_threads[kBatchClasses], cls_claim[kBatchClasses];
+  // start from the caller's table: its class CTA sizes and claim sizes are
+  // kept, its valid tiles are the starting point of the search
+  ct_batch_tiles cur;
+  memset(&cur, 0, sizeof(cur));
   for (int c = 0; c < kBatchClasses; ++c) {
-    cls_threads[c] = batch_valid_threads(tiles->class_threads[c]) ? tiles->class_threads[c] : 0;
-    cls_claim[c] = tiles->claim_items[c] >= 1 && tiles->claim_items[c] <= 8 ? tiles->claim_items[c] : 0;
+    cur.class_threads[c] = batch_valid_threads(tiles->class_threads[c]) ? tiles->class_threads[c] : 0;
+    cur.claim_items[c] =
+        tiles->claim_items[c] >= 1 && tiles->claim_items[c] <= 8 ? tiles->claim_items[c] : 0;
   }
-  memset(tiles, 0, sizeof(*tiles));
-  memcpy(tiles->class_threads, cls_threads, sizeof(cls_threads));
-  memcpy(tiles->claim_items, cls_claim, sizeof(cls_claim));
+  for (int sc = 0; sc < 2; ++sc)
+    for (int k = 1; k <= kMaxK; k += 2)
+      if (valid_tile(tiles->block_x[sc][k], tiles->tile_y[sc][k], k, class_threads(&cur, k))) {
+        cur.block_x[sc][k] = tiles->block_x[sc][k];
+        cur.tile_y[sc][k] = tiles->tile_y[sc][k];
+      }
   const ct_measure_options mo = resolve_options(opt);
   const ct_platform_ops ops = platform_ops();
-  // representative image of each bucket: the median output area
   std::vector<std::vector<int>> bucket(2 * (kMaxK + 1));
+  std::vector<std::vector<int>> klass(kBatchClasses);
   for (int i = 0; i < n; ++i) {
     if (items[i].out_h <= 0 || items[i].out_w <= 0) continue;
     if (items[i].k < 1 || items[i].k > kMaxK || !(items[i].k & 1)) return CT_EINVAL;
     bucket[size_class(items[i].out_h, items[i].out_w) * (kMaxK + 1) + items[i].k].push_back(i);
+    klass[batch_class_of(items[i].k)].push_back(i);
   }
   const int bxs[4] = {16, 32, 64, 128}, tys[4] = {1, 2, 4, 8};
   auto n_ty = [](int k) { return k <= kBatchMaxK8 ? 4 : 3; };
@@ -723,56 +729,59 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
     needed += bucket[q].empty() ? 0 : 4 * n_ty((int)(q % (kMaxK + 1)));
   *n_records = needed;
   if (records && cap < needed) return CT_ENOMEM;
-  for (int cls = 0; cls < 2; ++cls) {
+  // One bucket (size class, filter side) at a time, each candidate tile
+  // measured on the whole filter-side class the bucket belongs to, with the
+  // class's other buckets at their current tiles: a class launch's staging
+  // buffers and occupancy follow its largest tile, so a tile that is best
+  // for its bucket alone can slow the rest of its class (measured on the
+  // 256-image batch: tuning buckets alone gave a 9 % slower batch).
+  for (int c = 0; c < kBatchClasses; ++c) {
+    if (klass[c].empty()) continue;
+    std::vector<ct_batch_item> sub;
+    for (int i : klass[c]) sub.push_back(items[i]);
     for (int k = 1; k <= kMaxK; k += 2) {
-      std::vector<int>& v = bucket[cls * (kMaxK + 1) + k];
-      if (v.empty()) continue;
-      // every image of the bucket, as one batch: a launch the size of the
-      // bucket's share of the real batch (one median image alone measured
-      // launch and tail effects more than the tile, and its pick varied from
-      // run to run)
-      std::vector<ct_batch_item> sub;
-      for (int i : v) sub.push_back(items[i]);
-      std::vector<ct_record> recs;
-      for (int bx : bxs)
-        for (int qt = 0; qt < n_ty(k); ++qt) {
-          const int ty = tys[qt];
-          ct_batch_tiles t;
-          memset(&t, 0, sizeof(t));
-          memcpy(t.class_threads, cls_threads, sizeof(cls_threads));
-          memcpy(t.claim_items, cls_claim, sizeof(cls_claim));
-          if (bx > class_threads(&t, k)) continue;  // wider than the CTA
-          t.block_x[cls][k] = bx;
-          t.tile_y[cls][k] = ty;
-          ct_batch* b = nullptr;
-          int rc = ct_batch_create(sub.data(), (int)sub.size(), &t, &b);
-          if (rc != CT_OK) return rc;
-          MeasureUnit u;
-          u.kind = CT_UNIT_CONV;
-          u.work = b->flop;
-          u.launch = [b](cudaStream_t s) { return enqueue_batch(b, s); };
-          ct_record r;
-          rc = measure_unit(u, mo, ops, (cudaStream_t)stream, 0, &r);
-          ct_batch_destroy(b);
-          if (rc != CT_OK) return rc;
-          r.cfg.block_x = bx;
-          r.cfg.block_y = class_threads(&t, k) / bx;
-          r.cfg.tile_x = kBatchTileX;
-          r.cfg.tile_y = ty;
-          r.cfg.staging = CT_STAGE_SMEM;
-          r.cfg.filter_mem = CT_FILTER_SHARED;
-          r.cfg.vec_width = 4;
-          recs.push_back(r);
-          if (records) records[written] = r;
-          ++written;
-        }
-      int best = 0;
-      ct_select_best(recs.data(), (int)recs.size(), objective, nullptr, 0, &best);
-      if (best < 0) best = 0;
-      tiles->block_x[cls][k] = recs[best].cfg.block_x;
-      tiles->tile_y[cls][k] = recs[best].cfg.tile_y;
+      if (batch_class_of(k) != c) continue;
+      for (int sc = 0; sc < 2; ++sc) {
+        if (bucket[sc * (kMaxK + 1) + k].empty()) continue;
+        std::vector<ct_record> recs;
+        for (int bx : bxs)
+          for (int qt = 0; qt < n_ty(k); ++qt) {
+            const int ty = tys[qt];
+            ct_batch_tiles t = cur;
+            if (bx > class_threads(&t, k)) continue;  // wider than the CTA
+            t.block_x[sc][k] = bx;
+            t.tile_y[sc][k] = ty;
+            ct_batch* b = nullptr;
+            int rc = ct_batch_create(sub.data(), (int)sub.size(), &t, &b);
+            if (rc != CT_OK) return rc;
+            MeasureUnit u;
+            u.kind = CT_UNIT_CONV;
+            u.work = b->flop;
+            u.launch = [b](cudaStream_t s) { return enqueue_batch(b, s); };
+            ct_record r;
+            rc = measure_unit(u, mo, ops, (cudaStream_t)stream, 0, &r);
+            ct_batch_destroy(b);
+            if (rc != CT_OK) return rc;
+            r.cfg.block_x = bx;
+            r.cfg.block_y = class_threads(&t, k) / bx;
+            r.cfg.tile_x = kBatchTileX;
+            r.cfg.tile_y = ty;
+            r.cfg.staging = CT_STAGE_TMA;
+            r.cfg.filter_mem = CT_FILTER_SHARED;  // taps staged into shared memory
+            r.cfg.vec_width = 4;
+            recs.push_back(r);
+            if (records) records[written] = r;
+            ++written;
+          }
+        int best = 0;
+        ct_select_best(recs.data(), (int)recs.size(), objective, nullptr, 0, &best);
+        if (best < 0) best = 0;
+        cur.block_x[sc][k] = recs[best].cfg.block_x;
+        cur.tile_y[sc][k] = recs[best].cfg.tile_y;
+      }
     }
   }
+  *tiles = cur;
   *n_records = written;
   return CT_OK;
 }

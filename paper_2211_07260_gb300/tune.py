@@ -93,8 +93,13 @@ def tune_batched(objective="energy", window=0.3, out=None, n=256, seed=2, log=pr
         o = torch.empty((p.out_h, (p.out_w + 3) // 4 * 4), dtype=torch.float32, device="cuda")
         ents.append((d_in, p.filt, o, p.out_h, p.out_w))
     t0 = time.time()
+    # start from the device's current table (if any)
+    start = None
+    if out and os.path.exists(out):
+        raw = json.load(open(out)).get("batched_tiles", {}).get(api.device_info()["name"])
+        start = api.tiles_from_json(raw) if raw else None
     tiles, recs = api.batch_tune(ents, objective, api.measure_options(window_s=window,
-                                                                      warmup_s=0.1))
+                                                                      warmup_s=0.1), start=start)
     log(json.dumps(dict(batched_tiles=api.tiles_to_json(tiles), points=len(recs),
                         wall_s=time.time() - t0)))
     if out:
