@@ -17,9 +17,12 @@ At N = 1 the same line also carries, each with its own SM-clock record:
                                       configuration, graph-replayed and with
                                       L2 flushed, against min(FP32, AI x HBM);
   batched256                          the 256-image batch as one CUDA-graph
-                                      launch of the persistent kernels vs one
-                                      plain launch per image (GFLOP/s, GFLOP/J,
-                                      mixed roofline, FP64 oracle baseline);
+                                      launch (the batch's mode: one single-
+                                      image kernel per image over 16 graph
+                                      branches), the persistent class kernels'
+                                      graph, and one host-issued plain launch
+                                      per image (GFLOP/s, GFLOP/J, mixed
+                                      roofline, FP64 oracle baseline);
   serving                             Poisson requests through the continuous-
                                       batching server vs one plain kernel per
                                       request (p50 / p99, J per request).
@@ -312,9 +315,10 @@ def batched_oracle_baseline(probs, seconds):
 
 
 def measure_batched(args, world, local, steps, warmup, cpu_seconds):
-    """The 256-image batch: one CUDA-graph launch of the persistent class
-    kernels against one plain launch per image, timed by CUDA events and by
-    the library's energy window, with an SM-clock record."""
+    """The 256-image batch: one CUDA-graph launch (the batch's own mode, and
+    the persistent class kernels' graph beside it) against one host-issued
+    plain launch per image, timed by CUDA events and by the library's energy
+    window, with an SM-clock record."""
     import torch
 
     from paper_2211_07260_gb300 import api, synth
@@ -335,14 +339,18 @@ def measure_batched(args, world, local, steps, warmup, cpu_seconds):
         st = b.info()
         for _ in range(max(3, warmup)):
             b.run(stream)
+            b.run(stream, which="persistent")
         b.run_plain(stream)
         torch.cuda.synchronize()
         sampler.start()
         t_graph = all_max(world, sum(timed_steps(world, stream, steps, lambda: b.run(stream))))
+        t_pers = all_max(world, sum(timed_steps(
+            world, stream, steps, lambda: b.run(stream, which="persistent"))))
         t_plain = all_max(world, sum(timed_steps(world, stream, steps,
                                                  lambda: b.run_plain(stream))))
-        rb = b.measure(False, opts)
-        rp = b.measure(True, opts)
+        rb = b.measure("default", opts)
+        rq = b.measure("persistent", opts)
+        rp = b.measure("plain", opts)
         clocks = sampler.stop()
     # mixed roofline: per image the slower of its FLOP at the FP32 peak and
     # its bytes at the HBM copy rate
@@ -358,11 +366,19 @@ def measure_batched(args, world, local, steps, warmup, cpu_seconds):
         "workload": "256 images, sides log-uniform [256, 2048], odd k 3..17, seed 2",
         "images": st["n_images"], "work_items": st["n_items"], "class_launches": st["launches"],
         "persistent_ctas": st["grid"], "tiles_source": src, "gflop": st["flop"] / 1e9,
-        "l2": "inputs 0.78 GB > L2 (no flush needed)",
-        "graph": {"gflops": g_graph / 1e9, "ms_per_batch": t_graph * 1e3 / steps,
+        "l2": "inputs 0.78 GB > L2 (no flush needed)", "mode": st["mode_name"],
+        "graph": {"mode": st["mode_name"], "gflops": g_graph / 1e9,
+                  "ms_per_batch": t_graph * 1e3 / steps,
                   "gflops_energy_window": rb["gflops"], "gflop_per_j": rb["gflops_per_j"],
                   "power_w_mean": rb["power_w_mean"], "flags": rb["flags"],
-                  "gpu_launches_per_batch": st["launches"]},
+                  "gpu_launches_per_batch": (st["n_images"] if st["mode_name"] == "launches"
+                                             else st["launches"])},
+        "persistent_graph": {"gflops": st["flop"] * steps / t_pers / 1e9,
+                             "ms_per_batch": t_pers * 1e3 / steps,
+                             "gflops_energy_window": rq["gflops"],
+                             "gflop_per_j": rq["gflops_per_j"],
+                             "power_w_mean": rq["power_w_mean"], "flags": rq["flags"],
+                             "gpu_launches_per_batch": st["launches"]},
         "plain_per_image": {"gflops": st["flop"] * steps / t_plain / 1e9,
                             "ms_per_batch": t_plain * 1e3 / steps,
                             "gflops_energy_window": rp["gflops"],

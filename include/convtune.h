@@ -546,25 +546,39 @@ int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
                     int* best_index);
 
 
-/* ---- persistent batched correlation ------------------------------------- */
+/* ---- batched correlation -------------------------------------------------- */
 
 /*
- * Many correlations of uneven sizes and odd filter sides (1..17) in one
- * persistent launch per filter-side class (sides 1-7, 9-11, 13-17: separate
- * kernels so that each keeps its own register budget).  A plan copies the
- * taps and an image table to the device (library scratch, freed by
- * ct_batch_destroy), sorts the images by (filter side, size class) and
- * captures [work-counter reset + the persistent class kernels] into a CUDA
- * graph; ct_batch_run replays it (one host call and one graph launch per
- * batch).  CTAs of 256 threads, resident-occupancy x SM count of them per
- * class kernel, take output tiles from a global atomic counter; each tile
- * uses the tap order of the plain kernel, so outputs are bitwise identical
- * to ct_conv2d_run.  Tiles are 4 outputs wide per thread; per bucket
- * (size class: output area < or >= 512^2; filter side) the block width and
- * tile height come from ct_batch_tiles (0 or invalid entries: 32 x 8
- * threads, tile_y 2).  The plain comparison runs each image with the same
- * block and min(tile_y, 4).
+ * Many correlations of uneven sizes and odd filter sides (1..17) behind one
+ * host call and one CUDA-graph launch per batch.  A plan copies the taps and
+ * an image table to the device (library scratch, freed by ct_batch_destroy)
+ * and captures up to two graphs, both bitwise identical to ct_conv2d_run per
+ * image (every tile uses the plain kernel's tap order):
+ *
+ *  - persistent: [work-counter reset + one persistent kernel per filter-side
+ *    class] (sides 1-7, 9-11, 13-17: separate kernels so that each keeps its
+ *    own register budget); images sorted by (filter side, size class).  CTAs
+ *    of 256 threads, resident-occupancy x SM count of them per class kernel,
+ *    take output tiles from a global atomic counter.  Tiles are 4 outputs
+ *    wide per thread; per bucket (size class: output area < or >= 512^2;
+ *    filter side) the block width and tile height come from ct_batch_tiles
+ *    (0 or invalid entries: 32 x 8 threads, tile_y 2).
+ *  - launches: one single-image kernel per image (compile-time filter side,
+ *    taps in its parameter block), largest work first, round-robin over 16
+ *    parallel graph branches; per bucket block_x x block_y threads and
+ *    tile_y from the launch_* fields of ct_batch_tiles (0: 16 x 8, tile_y 4),
+ *    TMA staging where the input allows it.  Captured for batches of at most
+ *    CT_BATCH_LAUNCH_MAX_IMAGES images, unless the mode asked for is
+ *    CT_BATCH_PERSISTENT.
+ *
+ * ct_batch_run replays the batch's mode: ct_batch_tiles.mode, where
+ * CT_BATCH_AUTO takes the launches graph when it exists and the images
+ * average at least 65,536 outputs (each launch then fills a good part of the
+ * GPU), else the persistent graph.  The plain comparison runs each image
+ * with the persistent bucket's block and min(tile_y, 4), host-issued.
  */
+enum { CT_BATCH_AUTO = 0, CT_BATCH_PERSISTENT = 1, CT_BATCH_LAUNCHES = 2 };
+#define CT_BATCH_LAUNCH_MAX_IMAGES 1024
 typedef struct {
   const float* in;    /* device, padded input: out_h+k-1 rows of in_pitch   */
   long in_pitch;
@@ -583,6 +597,11 @@ typedef struct {
                            13-17: 64, 128 or 256 (0: 256)                    */
   int claim_items[3];   /* work items (consecutive tiles) per claim of the
                            persistent CTAs, per class: 1..8 (0: 2, 1, 1)     */
+  int launch_block_x[2][18]; /* launches graph, [size class][k]: 16, 32, 64,
+                                128 (0: 16)                                   */
+  int launch_block_y[2][18]; /* 1, 2, 4, 8 (0: 8); block_x x block_y <= 1024 */
+  int launch_tile_y[2][18];  /* 1, 2, 4 (0: 4)                               */
+  int mode;                  /* CT_BATCH_AUTO / _PERSISTENT / _LAUNCHES       */
 } ct_batch_tiles;
 
 typedef struct {
@@ -592,25 +611,36 @@ typedef struct {
   long smem_bytes;    /* dynamic shared memory per CTA (largest launch)     */
   double flop;        /* useful FLOP per batch                              */
   double bytes;       /* algorithmic bytes per batch (inputs, outputs, taps) */
-  int launches;       /* kernel launches per run: one persistent kernel per
-                         filter-side class present (sides 1-7, 9-11, 13-17) */
+  int launches;       /* kernel launches per persistent run: one persistent
+                         kernel per filter-side class present (sides 1-7,
+                         9-11, 13-17), more when parameter blocks fill up    */
+  int mode;           /* CT_BATCH_PERSISTENT or CT_BATCH_LAUNCHES: the graph
+                         ct_batch_run replays                                */
+  int has_launch_graph; /* 1: the launches graph was captured too            */
 } ct_batch_stats;
 
 typedef struct ct_batch ct_batch;  /* opaque plan */
 
 int ct_batch_create(const ct_batch_item* items, int n, const ct_batch_tiles* tiles_or_null,
                     ct_batch** out);
-/* Replay the captured batch on `stream` (asynchronous). */
+/* Replay the captured batch (its mode's graph) on `stream` (asynchronous). */
 int ct_batch_run(ct_batch* b, void* stream);
+/* What ct_batch_run_mode and ct_measure_batch run: the batch's own mode,
+   the plain comparison, the persistent graph, the launches graph
+   (CT_ENOTSUP when it was not captured). */
+enum { CT_BATCH_RUN_DEFAULT = 0, CT_BATCH_RUN_PLAIN = 1, CT_BATCH_RUN_PERSISTENT = 2,
+       CT_BATCH_RUN_LAUNCHES = 3 };
+int ct_batch_run_mode(ct_batch* b, int which, void* stream);
 /* The comparison: one ct_conv2d_run per image (bucket configuration, taps
    from the parameter space), in table order, on `stream`. */
 int ct_batch_run_plain(ct_batch* b, void* stream);
 int ct_batch_info(const ct_batch* b, ct_batch_stats* out);
 /* Waits for nothing; the caller must have synchronised work using b. */
 int ct_batch_destroy(ct_batch* b);
-/* Measure the batch (plain = 0: graph replays of the persistent launch;
-   plain = 1: host-issued plain launches, no graph), as ct_measure_conv. */
-int ct_measure_batch(ct_batch* b, int plain, const ct_measure_options* opt, void* stream,
+/* Measure the batch as ct_measure_conv: `which` is a CT_BATCH_RUN_* value
+   (graph replays for the graphs; host-issued launches, no graph, for the
+   plain comparison). */
+int ct_measure_batch(ct_batch* b, int which, const ct_measure_options* opt, void* stream,
                      ct_record* out);
 /*
  * Per-bucket tile tuning: for every (size class, filter side) present,

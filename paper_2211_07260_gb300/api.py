@@ -222,6 +222,7 @@ _SIGS = {
     "ct_batch_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "ct_batch_run": (c_int, [c_void_p, c_void_p]),
     "ct_batch_run_plain": (c_int, [c_void_p, c_void_p]),
+    "ct_batch_run_mode": (c_int, [c_void_p, c_int, c_void_p]),
     "ct_batch_info": (c_int, [c_void_p, c_void_p]),
     "ct_batch_destroy": (c_int, [c_void_p]),
     "ct_measure_batch": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
@@ -691,24 +692,37 @@ class CtBatchItem(ctypes.Structure):
                 ("out", c_void_p), ("out_pitch", c_long), ("out_h", c_int), ("out_w", c_int)]
 
 
+BATCH_MODES = {"auto": 0, "persistent": 1, "launches": 2}
+BATCH_RUNS = {"default": 0, "plain": 1, "persistent": 2, "launches": 3}
+
+
 class CtBatchTiles(ctypes.Structure):
     _fields_ = [("block_x", (c_int * 18) * 2), ("tile_y", (c_int * 18) * 2),
-                ("class_threads", c_int * 3), ("claim_items", c_int * 3)]
+                ("class_threads", c_int * 3), ("claim_items", c_int * 3),
+                ("launch_block_x", (c_int * 18) * 2), ("launch_block_y", (c_int * 18) * 2),
+                ("launch_tile_y", (c_int * 18) * 2), ("mode", c_int)]
 
     def to_dict(self) -> dict:
-        """{(size class, k): (block_x, tile_y)} plus {("threads", filter-side
-        class): CTA size} and {("claim", filter-side class): items per claim}
-        for the classes where they are set."""
+        """{(size class, k): (block_x, tile_y)} of the persistent kernels,
+        {("threads", filter-side class): CTA size}, {("claim", filter-side
+        class): items per claim}, {("L<size class>", k): (block_x, block_y,
+        tile_y)} of the launches graph and {("mode", 0): mode}, where set."""
         out = {}
         for cls in (0, 1):
             for k in range(18):
                 if self.block_x[cls][k]:
                     out[(cls, k)] = (self.block_x[cls][k], self.tile_y[cls][k])
+                if self.launch_block_x[cls][k]:
+                    out[(f"L{cls}", k)] = (self.launch_block_x[cls][k],
+                                           self.launch_block_y[cls][k],
+                                           self.launch_tile_y[cls][k])
         for c in range(3):
             if self.class_threads[c]:
                 out[("threads", c)] = self.class_threads[c]
             if self.claim_items[c]:
                 out[("claim", c)] = self.claim_items[c]
+        if self.mode:
+            out[("mode", 0)] = self.mode
         return out
 
     @classmethod
@@ -719,6 +733,12 @@ class CtBatchTiles(ctypes.Structure):
                 t.class_threads[int(key[1])] = int(val)
             elif key[0] == "claim":
                 t.claim_items[int(key[1])] = int(val)
+            elif key[0] == "mode":
+                t.mode = int(val)
+            elif isinstance(key[0], str) and key[0] in ("L0", "L1"):
+                c, k = int(key[0][1]), int(key[1])
+                (t.launch_block_x[c][k], t.launch_block_y[c][k],
+                 t.launch_tile_y[c][k]) = (int(v) for v in val)
             else:
                 c, k = key
                 t.block_x[c][k], t.tile_y[c][k] = val
@@ -727,26 +747,28 @@ class CtBatchTiles(ctypes.Structure):
 
 def tiles_from_json(raw: dict) -> dict:
     """Tiles dict from its JSON form ({"c,k": [bx, ty], "threads,c": n,
-    "claim,c": n})."""
+    "claim,c": n, "Lc,k": [bx, by, ty], "mode,0": n})."""
     out = {}
     for key, val in raw.items():
         a, b = key.split(",")
-        if a in ("threads", "claim"):
+        if a in ("threads", "claim", "mode"):
             out[(a, int(b))] = int(val)
+        elif a in ("L0", "L1"):
+            out[(a, int(b))] = tuple(val)
         else:
             out[(int(a), int(b))] = tuple(val)
     return out
 
 
 def tiles_to_json(tiles: dict) -> dict:
-    return {f"{a},{b}": (val if a in ("threads", "claim") else list(val))
+    return {f"{a},{b}": (val if a in ("threads", "claim", "mode") else list(val))
             for (a, b), val in tiles.items()}
 
 
 class CtBatchStats(ctypes.Structure):
     _fields_ = [("n_images", c_int), ("n_items", ctypes.c_longlong), ("grid", c_int),
                 ("smem_bytes", c_long), ("flop", c_double), ("bytes", c_double),
-                ("launches", c_int)]
+                ("launches", c_int), ("mode", c_int), ("has_launch_graph", c_int)]
 
 
 def batch_items(entries):
@@ -764,20 +786,31 @@ def batch_items(entries):
     return arr, keep
 
 
-class Batch:
-    """A persistent batched plan (ct_batch_create); destroy() or use as a
-    context manager."""
+def _batch_run_code(which) -> int:
+    if isinstance(which, bool):  # measure(True): the plain comparison
+        return BATCH_RUNS["plain"] if which else BATCH_RUNS["default"]
+    return BATCH_RUNS[which] if isinstance(which, str) else int(which)
 
-    def __init__(self, entries, tiles: dict | None = None):
+
+class Batch:
+    """A batched plan (ct_batch_create); destroy() or use as a context
+    manager.  mode: "auto", "persistent" or "launches" (overrides the tiles'
+    mode)."""
+
+    def __init__(self, entries, tiles: dict | None = None, mode: str | None = None):
         self._items, self._keep = batch_items(entries)
         self._h = c_void_p(0)
         t = CtBatchTiles.from_dict(tiles) if tiles else None
+        if mode is not None:
+            t = t if t is not None else CtBatchTiles()
+            t.mode = BATCH_MODES[mode]
         _check(lib().ct_batch_create(self._items, len(entries),
                                      ctypes.byref(t) if t is not None else None,
                                      ctypes.byref(self._h)), "ct_batch_create")
 
-    def run(self, stream=None):
-        _check(lib().ct_batch_run(self._h, c_void_p(stream_handle(stream))), "ct_batch_run")
+    def run(self, stream=None, which="default"):
+        _check(lib().ct_batch_run_mode(self._h, _batch_run_code(which),
+                                       c_void_p(stream_handle(stream))), "ct_batch_run_mode")
 
     def run_plain(self, stream=None):
         _check(lib().ct_batch_run_plain(self._h, c_void_p(stream_handle(stream))),
@@ -786,12 +819,16 @@ class Batch:
     def info(self) -> dict:
         st = CtBatchStats()
         _check(lib().ct_batch_info(self._h, ctypes.byref(st)), "ct_batch_info")
-        return {k: getattr(st, k) for k, _ in CtBatchStats._fields_}
+        d = {k: getattr(st, k) for k, _ in CtBatchStats._fields_}
+        d["mode_name"] = {1: "persistent", 2: "launches"}.get(d["mode"], "?")
+        return d
 
-    def measure(self, plain=False, opts=None, stream=None) -> dict:
+    def measure(self, which="default", opts=None, stream=None) -> dict:
+        """which: "default" (the batch's mode), "plain", "persistent",
+        "launches" (True / False: plain / default)."""
         r = CtRecord()
         o = opts or measure_options()
-        _check(lib().ct_measure_batch(self._h, int(bool(plain)), ctypes.byref(o),
+        _check(lib().ct_measure_batch(self._h, _batch_run_code(which), ctypes.byref(o),
                                       c_void_p(stream_handle(stream)), ctypes.byref(r)),
                "ct_measure_batch")
         return r.to_dict()

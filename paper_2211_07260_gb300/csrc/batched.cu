@@ -264,6 +264,9 @@ const void* batched_kernel_fn(int cls) {
 namespace {
 
 constexpr size_t kBatchBranches = 8;  // parallel branches of a captured batch graph
+// Parallel branches of the launches graph (GB300, 256-image batch, one
+// single-image launch per image: 16 branches 979 us, 8 branches 1008 us).
+constexpr size_t kBatchLaunchBranches = 16;
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -457,8 +460,18 @@ struct ct_batch {
   // so that one launch's last tiles overlap the next launch's first ones
   std::vector<cudaStream_t> branches;
   std::vector<cudaEvent_t> events;  // one per branch + the fork
+  // launches graph: one single-image kernel per image, largest work first
+  std::vector<ct_problem> lprob;
+  std::vector<ct_config> lcfg;
+  cudaGraphExec_t exec_launch = nullptr;
+  std::vector<cudaStream_t> lbranches;
+  std::vector<cudaEvent_t> levents;  // one per branch + the fork
+  int mode = CT_BATCH_PERSISTENT;    // the graph ct_batch_run replays
   ~ct_batch() {
     if (exec) cudaGraphExecDestroy(exec);
+    if (exec_launch) cudaGraphExecDestroy(exec_launch);
+    for (cudaStream_t bs : lbranches) cudaStreamDestroy(bs);
+    for (cudaEvent_t ev : levents) cudaEventDestroy(ev);
     for (cudaStream_t bs : branches) cudaStreamDestroy(bs);
     for (cudaEvent_t ev : events) cudaEventDestroy(ev);
     if (capture_stream) cudaStreamDestroy(capture_stream);
@@ -508,6 +521,71 @@ int enqueue_plain(ct_batch* b, cudaStream_t s) {
     const int rc = ct_conv2d_run(&p, &c, s);
     if (rc != CT_OK) return rc;
   }
+  return CT_OK;
+}
+
+// Launches mode, one image: the bucket's block and tile height (defaults
+// 16 x 8 threads, tile_y 4: the single-image kernel's energy optimum at
+// 4096^2 / 17 x 17), taps in the parameter block, TMA staging with 4-wide
+// loads where the buffers allow it, else shared-memory staging with the
+// widest loads they allow.
+int launch_config(const ct_batch_item& it, const float* taps, const ct_batch_tiles* tiles,
+                  ct_problem* p, ct_config* c) {
+  p->in = it.in;
+  p->in_pitch = it.in_pitch;
+  p->filt = taps;
+  p->fh = p->fw = it.k;
+  p->out = it.out;
+  p->out_pitch = it.out_pitch;
+  p->out_h = it.out_h;
+  p->out_w = it.out_w;
+  int bx = 16, by = 8, ty = 4;
+  if (tiles) {
+    const int cls = size_class(it.out_h, it.out_w);
+    const int tbx = tiles->launch_block_x[cls][it.k], tby = tiles->launch_block_y[cls][it.k];
+    const int tty = tiles->launch_tile_y[cls][it.k];
+    if ((tbx == 16 || tbx == 32 || tbx == 64 || tbx == 128) &&
+        (tby == 1 || tby == 2 || tby == 4 || tby == 8) && (tty == 1 || tty == 2 || tty == 4)) {
+      bx = tbx;
+      by = tby;
+      ty = tty;
+    }
+  }
+  const int stage[5] = {CT_STAGE_TMA, CT_STAGE_SMEM, CT_STAGE_SMEM, CT_STAGE_SMEM,
+                        CT_STAGE_DIRECT};
+  const int vec[5] = {4, 4, 2, 1, 1};
+  int rc = CT_ECONFIG;
+  for (int q = 0; q < 5; ++q) {
+    c->block_x = bx;
+    c->block_y = by;
+    c->tile_x = kBatchTileX;
+    c->tile_y = ty;
+    c->staging = stage[q];
+    c->filter_mem = CT_FILTER_CONST;
+    c->vec_width = vec[q];
+    if ((rc = ct_conv2d_check(p, c, nullptr, 0)) == CT_OK) return CT_OK;
+  }
+  return rc;
+}
+
+// The launches graph's work: fork `s` to the branches, one single-image
+// launch per image (largest work first) on branch n % branches, join.
+int enqueue_launches(ct_batch* b, cudaStream_t s) {
+  const int nb = (int)b->lbranches.size();
+  if (nb == 0) return CT_ENOTSUP;
+  cudaError_t e = cudaEventRecord(b->levents[nb], s);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int q = 0; q < nb; ++q)
+    if ((e = cudaStreamWaitEvent(b->lbranches[q], b->levents[nb], 0)) != cudaSuccess)
+      return cuda_status(e);
+  for (size_t n = 0; n < b->lprob.size(); ++n) {
+    const int rc = ct_conv2d_run(&b->lprob[n], &b->lcfg[n], b->lbranches[n % nb]);
+    if (rc != CT_OK) return rc;
+  }
+  for (int q = 0; q < nb; ++q)
+    if ((e = cudaEventRecord(b->levents[q], b->lbranches[q])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, b->levents[q], 0)) != cudaSuccess)
+      return cuda_status(e);
   return CT_OK;
 }
 
@@ -586,7 +664,64 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
     return cuda_status(e);
   if ((e = cudaMalloc(&b->d_counter, kBatchCounterBytes)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(b->d_counter, 0, kBatchCounterBytes)) != cudaSuccess) return cuda_status(e);
+  // launches mode: every image's problem and configuration, largest work
+  // first (stable: equal work keeps input order)
+  if (b->host_images.size() <= (size_t)CT_BATCH_LAUNCH_MAX_IMAGES) {
+    std::vector<int> by_work(b->order);
+    std::stable_sort(by_work.begin(), by_work.end(), [&](int x, int y) {
+      const double wx = (double)items[x].k * items[x].k * items[x].out_h * items[x].out_w;
+      const double wy = (double)items[y].k * items[y].k * items[y].out_h * items[y].out_w;
+      return wx > wy;
+    });
+    for (int i : by_work) {
+      ct_problem p;
+      ct_config c;
+      const int rc2 = launch_config(items[i], b->taps[i].data(), tiles, &p, &c);
+      if (rc2 != CT_OK) return rc2;
+      b->lprob.push_back(p);
+      b->lcfg.push_back(c);
+    }
+  }
   return CT_OK;
+}
+
+// Capture the launches graph (batches of at most CT_BATCH_LAUNCH_MAX_IMAGES
+// images).
+int capture_launches(ct_batch* b) {
+  if (b->lprob.empty()) return CT_OK;
+  cudaError_t e;
+  const size_t nb = std::min<size_t>(b->lprob.size(), kBatchLaunchBranches);
+  for (size_t q = 0; q < nb; ++q) {
+    cudaStream_t bs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_status(e);
+    b->lbranches.push_back(bs);
+  }
+  for (size_t q = 0; q <= nb; ++q) {
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_status(e);
+    b->levents.push_back(ev);
+  }
+  // one uncaptured run first: first-use kernel attributes and module loads
+  // happen outside the capture
+  int rc = enqueue_launches(b, b->capture_stream);
+  if (rc != CT_OK) return rc;
+  if ((e = cudaStreamSynchronize(b->capture_stream)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return cuda_status(e);
+  rc = enqueue_launches(b, b->capture_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->capture_stream, &g);
+  if (rc != CT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGraphInstantiate(&b->exec_launch, g, 0);
+  cudaGraphDestroy(g);
+  return cuda_status(e);
 }
 
 int capture_batch(ct_batch* b) {
@@ -637,6 +772,20 @@ int ct_batch_create(const ct_batch_item* items, int n, const ct_batch_tiles* til
   cudaError_t e = cudaGetDevice(&b->device);
   int rc = e == cudaSuccess ? build_batch(items, n, tiles, b) : cuda_status(e);
   if (rc == CT_OK) rc = capture_batch(b);
+  const int req = tiles ? tiles->mode : CT_BATCH_AUTO;
+  if (rc == CT_OK && req != CT_BATCH_PERSISTENT) rc = capture_launches(b);
+  if (rc == CT_OK) {
+    double px = 0;
+    for (const BatchImage& im : b->host_images) px += (double)im.out_h * im.out_w;
+    const bool big = !b->host_images.empty() && px >= 65536.0 * b->host_images.size();
+    if (req == CT_BATCH_LAUNCHES)
+      rc = b->exec_launch || b->host_images.empty() ? CT_OK : CT_ENOTSUP;
+    else if (req != CT_BATCH_AUTO && req != CT_BATCH_PERSISTENT)
+      rc = CT_EINVAL;
+    b->mode = (req == CT_BATCH_LAUNCHES || (req == CT_BATCH_AUTO && big)) && b->exec_launch
+                  ? CT_BATCH_LAUNCHES
+                  : CT_BATCH_PERSISTENT;
+  }
   if (rc != CT_OK) {
     delete b;
     return rc;
@@ -648,7 +797,27 @@ int ct_batch_create(const ct_batch_item* items, int n, const ct_batch_tiles* til
 int ct_batch_run(ct_batch* b, void* stream) {
   if (!b) return CT_EINVAL;
   if (b->n_items == 0) return CT_OK;
-  return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return cuda_status(cudaGraphLaunch(b->mode == CT_BATCH_LAUNCHES ? b->exec_launch : b->exec,
+                                     (cudaStream_t)stream));
+}
+
+int ct_batch_run_mode(ct_batch* b, int which, void* stream) {
+  if (!b) return CT_EINVAL;
+  switch (which) {
+    case CT_BATCH_RUN_DEFAULT:
+      return ct_batch_run(b, stream);
+    case CT_BATCH_RUN_PLAIN:
+      return enqueue_plain(b, (cudaStream_t)stream);
+    case CT_BATCH_RUN_PERSISTENT:
+      if (b->n_items == 0) return CT_OK;
+      return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    case CT_BATCH_RUN_LAUNCHES:
+      if (b->n_items == 0) return CT_OK;
+      if (!b->exec_launch) return CT_ENOTSUP;
+      return cuda_status(cudaGraphLaunch(b->exec_launch, (cudaStream_t)stream));
+    default:
+      return CT_EINVAL;
+  }
 }
 
 int ct_batch_run_plain(ct_batch* b, void* stream) {
@@ -665,6 +834,8 @@ int ct_batch_info(const ct_batch* b, ct_batch_stats* st) {
   st->smem_bytes = (long)b->smem;
   st->flop = b->flop;
   st->launches = (int)b->plan.launches.size();
+  st->mode = b->mode;
+  st->has_launch_graph = b->exec_launch ? 1 : 0;
   for (const BatchImage& im : b->host_images)
     st->bytes += 4.0 * ((double)im.in_h * im.in_w + (double)im.out_h * im.out_w + im.k * im.k);
   return CT_OK;
@@ -677,16 +848,22 @@ int ct_batch_destroy(ct_batch* b) {
   return CT_OK;
 }
 
-int ct_measure_batch(ct_batch* b, int plain, const ct_measure_options* opt, void* stream,
+int ct_measure_batch(ct_batch* b, int which, const ct_measure_options* opt, void* stream,
                      ct_record* out) {
   if (!b || !out) return CT_EINVAL;
   if (b->n_items == 0) return CT_EINVAL;
+  if (which == CT_BATCH_RUN_DEFAULT)
+    which = b->mode == CT_BATCH_LAUNCHES ? CT_BATCH_RUN_LAUNCHES : CT_BATCH_RUN_PERSISTENT;
+  if (which == CT_BATCH_RUN_LAUNCHES && !b->exec_launch) return CT_ENOTSUP;
+  if (which < CT_BATCH_RUN_PLAIN || which > CT_BATCH_RUN_LAUNCHES) return CT_EINVAL;
   MeasureUnit u;
   u.kind = CT_UNIT_CONV;
   u.work = b->flop;
-  u.eager = plain != 0;
-  if (plain)
+  u.eager = which == CT_BATCH_RUN_PLAIN;
+  if (which == CT_BATCH_RUN_PLAIN)
     u.launch = [b](cudaStream_t s) { return enqueue_plain(b, s); };
+  else if (which == CT_BATCH_RUN_LAUNCHES)
+    u.launch = [b](cudaStream_t s) { return enqueue_launches(b, s); };
   else
     u.launch = [b](cudaStream_t s) { return enqueue_batch(b, s); };
   return measure_unit(u, resolve_options(opt), platform_ops(), (cudaStream_t)stream, 0, out);
@@ -701,6 +878,11 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
   // kept, its valid tiles are the starting point of the search
   ct_batch_tiles cur;
   memset(&cur, 0, sizeof(cur));
+  // (the launches-mode fields and the mode pass through unchanged)
+  memcpy(cur.launch_block_x, tiles->launch_block_x, sizeof(cur.launch_block_x));
+  memcpy(cur.launch_block_y, tiles->launch_block_y, sizeof(cur.launch_block_y));
+  memcpy(cur.launch_tile_y, tiles->launch_tile_y, sizeof(cur.launch_tile_y));
+  cur.mode = tiles->mode;
   for (int c = 0; c < kBatchClasses; ++c) {
     cur.class_threads[c] = batch_valid_threads(tiles->class_threads[c]) ? tiles->class_threads[c] : 0;
     cur.claim_items[c] =
@@ -748,6 +930,7 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
           for (int qt = 0; qt < n_ty(k); ++qt) {
             const int ty = tys[qt];
             ct_batch_tiles t = cur;
+            t.mode = CT_BATCH_PERSISTENT;  // (no launches graph to capture)
             if (bx > class_threads(&t, k)) continue;  // wider than the CTA
             t.block_x[sc][k] = bx;
             t.tile_y[sc][k] = ty;

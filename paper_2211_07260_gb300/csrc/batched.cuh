@@ -236,12 +236,18 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& a, const BatchImage&
       if (param_taps) {
         // taps from the parameter block (constant bank), as in the single-image
         // kernel's ring
-        const float* wrow = a.w + im.tap_off;
+        const float4* wrow = reinterpret_cast<const float4*>(a.w + im.tap_off);
         accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(
             acc, [&](int r) { return sbase + r * pitch; },
             [&](int j, float(&w)[KP]) {
 #pragma unroll
-              for (int i = 0; i < K; ++i) w[i] = wrow[j * KP + i];
+              for (int i = 0; i < KP; i += 4) {
+                const float4 q = wrow[(j * KP + i) / 4];
+                w[i] = q.x;
+                w[i + 1] = q.y;
+                w[i + 2] = q.z;
+                w[i + 3] = q.w;
+              }
             });
       } else {
         accumulate_tile_ring<K, TX, TY, RingSchedule::kTested>(

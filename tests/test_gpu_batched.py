@@ -29,8 +29,9 @@ def mixed_problems(n=40, seed=5):
     return probs
 
 
+@pytest.mark.parametrize("mode", ["persistent", "launches"])
 @pytest.mark.parametrize("tiles", [None, "varied", "tall"])
-def test_batched_equals_plain_bitwise_and_oracle(tiles):
+def test_batched_equals_plain_bitwise_and_oracle(tiles, mode):
     probs = mixed_problems()
     t = None
     if tiles == "varied":
@@ -38,14 +39,18 @@ def test_batched_equals_plain_bitwise_and_oracle(tiles):
         for i, k in enumerate(range(1, 18, 2)):
             t[(0, k)] = ((16, 32, 64, 128)[i % 4], (1, 2, 4)[i % 3])
             t[(1, k)] = ((128, 64, 32, 16)[i % 4], (4, 1, 2)[i % 3])
+        # launches graph: per-bucket single-image blocks and tile heights
+        for i, k in enumerate(range(1, 18, 2)):
+            t[("L0", k)] = ((16, 32, 64, 128)[i % 4], (8, 4, 2, 1)[i % 4], (4, 2, 1)[i % 3])
     elif tiles == "tall":
         # 8-row tiles (filter sides <= 3 only; larger sides fall back to the
         # default tile)
         t = {(c, k): (32 if k < 5 else 64, 8) for c in (0, 1) for k in range(1, 18, 2)}
     ents, outs = device_entries(probs)
     ents_p, outs_p = device_entries(probs)
-    with api.Batch(ents, t) as b, api.Batch(ents_p, t) as bp:
+    with api.Batch(ents, t, mode=mode) as b, api.Batch(ents_p, t, mode="persistent") as bp:
         st = b.info()
+        assert st["mode_name"] == mode and st["has_launch_graph"] == (mode == "launches")
         # one persistent kernel per filter-side class, each grid capped by its items
         assert st["n_images"] == len(probs) and st["n_items"] >= st["grid"] > 0
         classes = {0 if p.filt.shape[0] <= 7 else 1 if p.filt.shape[0] <= 11 else 2 for p in probs}
@@ -85,16 +90,24 @@ def test_empty_images_and_errors():
 def test_workload_256_images_oracle_parity():
     probs = synth.batch_problems(256, seed=2)
     ents, outs = device_entries(probs)
-    with api.Batch(ents) as b:
-        b.run()
-        torch.cuda.synchronize()
+    ents_q, outs_q = device_entries(probs)
+    with api.Batch(ents) as b, api.Batch(ents_q) as bq:
         st = b.info()
+        # images of this workload average ~0.7 M outputs: the automatic mode
+        # replays the launches graph
+        assert st["mode_name"] == "launches" and st["has_launch_graph"] == 1
+        b.run()
+        bq.run(which="persistent")
+        torch.cuda.synchronize()
     flop = sum(2 * p.fh * p.fw * p.out_h * p.out_w for p in probs)
     assert st["flop"] == pytest.approx(flop)
     worst = 0.0
-    for p, o in zip(probs, outs):
-        worst = max(worst, max_rel_err(o.cpu().numpy()[:, :p.out_w], oracle_ref(p)))
+    for p, o, oq in zip(probs, outs, outs_q):
+        a = o.cpu().numpy()[:, :p.out_w]
+        assert np.array_equal(a, oq.cpu().numpy()[:, :p.out_w])  # both graphs, same bits
+        worst = max(worst, max_rel_err(a, oracle_ref(p)))
     assert worst <= MAX_REL
+    assert api.status_read(clear=True) == 0
 
 
 def test_bucket_tuning_and_measurement():
@@ -108,10 +121,14 @@ def test_bucket_tuning_and_measurement():
     for (cls, k), (bx, ty) in tiles.items():
         assert bx in (16, 32, 64, 128) and ty in ((1, 2, 4, 8) if k <= 3 else (1, 2, 4))
     with api.Batch(ents, tiles) as b:
-        rb = b.measure(False, api.measure_options(window_s=0.2, warmup_s=0.05))
-        rp = b.measure(True, api.measure_options(window_s=0.2, warmup_s=0.05))
-        assert rb["gflops"] > 0 and rp["gflops"] > 0
-        assert rb["energy_j"] > 0 and rp["energy_j"] > 0
+        o = api.measure_options(window_s=0.2, warmup_s=0.05)
+        recs_m = {w: b.measure(w, o) for w in ("default", "plain", "persistent", "launches")}
+        for r in recs_m.values():
+            assert r["gflops"] > 0 and r["energy_j"] > 0
+    with api.Batch(ents, tiles, mode="persistent") as b:
+        assert b.info()["has_launch_graph"] == 0
+        with pytest.raises(api.ConvTuneError):
+            b.measure("launches", o)
     torch.cuda.synchronize()
     for p, o in zip(probs, outs):
         assert max_rel_err(o.cpu().numpy()[:, :p.out_w], oracle_ref(p)) <= MAX_REL
@@ -129,6 +146,8 @@ def test_many_images_fill_every_parameter_block_then_fall_back():
     with api.Batch(ents, None) as b, api.Batch(ents_p, None) as bp:
         st = b.info()
         assert st["launches"] == 254
+        # too many images for a launches graph: the persistent kernels run
+        assert st["mode_name"] == "persistent" and st["has_launch_graph"] == 0
         b.run()
         bp.run_plain()
         torch.cuda.synchronize()
