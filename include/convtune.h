@@ -657,6 +657,19 @@ int ct_measure_batch(ct_batch* b, int which, const ct_measure_options* opt, void
 int ct_batch_tune(const ct_batch_item* items, int n, int objective,
                   const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,
                   ct_record* records, int cap, int* n_records);
+/*
+ * Per-bucket tuning of the launches graph: for every (size class, filter
+ * side) present, nine single-image configurations (block_x, block_y,
+ * tile_y) in {(16,8,4), (32,4,4), (32,2,4), (16,4,4), (64,2,4), (32,8,2),
+ * (32,4,2), (64,4,2), (128,2,2)} are measured, each as a launches graph of
+ * the bucket's images, and the objective's best goes to the launch_* fields
+ * of `tiles` (its other fields are kept).  records (optional: 9 per bucket)
+ * receive the measurements, with the configuration the bucket's first image
+ * ran (TMA staging, or its fallback).
+ */
+int ct_batch_tune_launches(const ct_batch_item* items, int n, int objective,
+                           const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,
+                           ct_record* records, int cap, int* n_records);
 
 
 /* ---- batched correlation that allocates nothing -------------------------- */

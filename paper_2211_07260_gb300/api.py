@@ -228,6 +228,8 @@ _SIGS = {
     "ct_measure_batch": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ct_batch_tune": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_int, c_void_p]),
+    "ct_batch_tune_launches": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_int, c_void_p]),
     "ct_batch_run_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "ct_batch_noalloc_status": (c_int, [c_void_p, c_int, c_void_p]),
     "ct_server_create": (c_int, [c_void_p, c_void_p]),
@@ -862,6 +864,24 @@ def batch_tune(entries, objective="energy", opts=None, stream=None, class_thread
     _check(lib().ct_batch_tune(items, len(entries), obj, ctypes.byref(o),
                                c_void_p(stream_handle(stream)), ctypes.byref(t), recs, cap,
                                ctypes.byref(n)), "ct_batch_tune")
+    return t.to_dict(), [recs[i].to_dict() for i in range(n.value)]
+
+
+def batch_tune_launches(entries, objective="energy", opts=None, stream=None,
+                        start: dict | None = None):
+    """Per-bucket single-image configurations of the launches graph
+    (ct_batch_tune_launches): (tiles dict, records); start: optional tiles
+    dict whose other entries are kept."""
+    items, keep = batch_items(entries)
+    t = CtBatchTiles.from_dict(start) if start else CtBatchTiles()
+    cap = 9 * 2 * 18
+    recs = (CtRecord * cap)()
+    n = c_int(0)
+    obj = OBJECTIVES[objective] if isinstance(objective, str) else int(objective)
+    o = opts or measure_options()
+    _check(lib().ct_batch_tune_launches(items, len(entries), obj, ctypes.byref(o),
+                                        c_void_p(stream_handle(stream)), ctypes.byref(t), recs,
+                                        cap, ctypes.byref(n)), "ct_batch_tune_launches")
     return t.to_dict(), [recs[i].to_dict() for i in range(n.value)]
 
 

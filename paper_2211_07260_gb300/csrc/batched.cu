@@ -267,6 +267,13 @@ constexpr size_t kBatchBranches = 8;  // parallel branches of a captured batch g
 // Parallel branches of the launches graph (GB300, 256-image batch, one
 // single-image launch per image: 16 branches 979 us, 8 branches 1008 us).
 constexpr size_t kBatchLaunchBranches = 16;
+// Launches-mode candidates of the per-bucket tuner: (block_x, block_y,
+// tile_y), 128 or 256 threads and 4-wide tiles, as in the single-image
+// kernel's fastest configurations (4096^2 / 17 x 17 and 1024^2 / 7 x 7).
+constexpr int kLaunchCandidates = 9;
+constexpr int kLaunchCand[kLaunchCandidates][3] = {
+    {16, 8, 4}, {32, 4, 4}, {32, 2, 4}, {16, 4, 4}, {64, 2, 4},
+    {32, 8, 2}, {32, 4, 2}, {64, 4, 2}, {128, 2, 2}};
 
 inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -964,6 +971,64 @@ int ct_batch_tune(const ct_batch_item* items, int n, int objective,
       }
     }
   }
+  *tiles = cur;
+  *n_records = written;
+  return CT_OK;
+}
+
+int ct_batch_tune_launches(const ct_batch_item* items, int n, int objective,
+                           const ct_measure_options* opt, void* stream, ct_batch_tiles* tiles,
+                           ct_record* records, int cap, int* n_records) {
+  if (!items || n <= 0 || !tiles || !n_records) return CT_EINVAL;
+  if (objective < CT_OBJ_TIME || objective > CT_OBJ_GFLOPS_PER_W) return CT_EINVAL;
+  std::vector<std::vector<int>> bucket(2 * (kMaxK + 1));
+  for (int i = 0; i < n; ++i) {
+    if (items[i].out_h <= 0 || items[i].out_w <= 0) continue;
+    if (items[i].k < 1 || items[i].k > kMaxK || !(items[i].k & 1)) return CT_EINVAL;
+    bucket[size_class(items[i].out_h, items[i].out_w) * (kMaxK + 1) + items[i].k].push_back(i);
+  }
+  int needed = 0;
+  for (const auto& v : bucket) needed += v.empty() ? 0 : kLaunchCandidates;
+  *n_records = needed;
+  if (records && cap < needed) return CT_ENOMEM;
+  const ct_measure_options mo = resolve_options(opt);
+  ct_batch_tiles cur = *tiles;
+  int written = 0;
+  for (int sc = 0; sc < 2; ++sc)
+    for (int k = 1; k <= kMaxK; k += 2) {
+      const std::vector<int>& v = bucket[sc * (kMaxK + 1) + k];
+      if (v.empty()) continue;
+      std::vector<ct_batch_item> sub;
+      for (int i : v) sub.push_back(items[i]);
+      std::vector<ct_record> recs;
+      for (int q = 0; q < kLaunchCandidates; ++q) {
+        ct_batch_tiles t = cur;
+        t.mode = CT_BATCH_LAUNCHES;
+        t.launch_block_x[sc][k] = kLaunchCand[q][0];
+        t.launch_block_y[sc][k] = kLaunchCand[q][1];
+        t.launch_tile_y[sc][k] = kLaunchCand[q][2];
+        ct_batch* b = nullptr;
+        int rc = ct_batch_create(sub.data(), (int)sub.size(), &t, &b);
+        if (rc != CT_OK) return rc;
+        ct_record r;
+        rc = ct_measure_batch(b, CT_BATCH_RUN_LAUNCHES, &mo, stream, &r);
+        // the configuration the bucket's first image ran with (its staging
+        // may have fallen back from TMA)
+        const ct_config c = b->lcfg.empty() ? ct_config{} : b->lcfg.front();
+        ct_batch_destroy(b);
+        if (rc != CT_OK) return rc;
+        r.cfg = c;
+        recs.push_back(r);
+        if (records) records[written] = r;
+        ++written;
+      }
+      int best = 0;
+      ct_select_best(recs.data(), (int)recs.size(), objective, nullptr, 0, &best);
+      if (best < 0) best = 0;
+      cur.launch_block_x[sc][k] = kLaunchCand[best][0];
+      cur.launch_block_y[sc][k] = kLaunchCand[best][1];
+      cur.launch_tile_y[sc][k] = kLaunchCand[best][2];
+    }
   *tiles = cur;
   *n_records = written;
   return CT_OK;

@@ -82,9 +82,11 @@ def run(workload, space="basic", objective="energy", window=0.3, prefilter=0, ca
     return summary, recs
 
 
-def tune_batched(objective="energy", window=0.3, out=None, n=256, seed=2, log=print):
-    """Per-bucket tiles of the batched workload (ct_batch_tune) into the
-    tuned-configuration table."""
+def tune_batched(objective="energy", window=0.3, out=None, n=256, seed=2, log=print,
+                 modes=("persistent", "launches")):
+    """Per-bucket tiles of the batched workload into the tuned-configuration
+    table: the persistent kernels' tiles (ct_batch_tune) and the launches
+    graph's single-image configurations (ct_batch_tune_launches)."""
     import torch
     probs = synth.batch_problems(n, seed)
     ents = []
@@ -98,8 +100,14 @@ def tune_batched(objective="energy", window=0.3, out=None, n=256, seed=2, log=pr
     if out and os.path.exists(out):
         raw = json.load(open(out)).get("batched_tiles", {}).get(api.device_info()["name"])
         start = api.tiles_from_json(raw) if raw else None
-    tiles, recs = api.batch_tune(ents, objective, api.measure_options(window_s=window,
-                                                                      warmup_s=0.1), start=start)
+    mo = api.measure_options(window_s=window, warmup_s=0.1)
+    tiles, recs = start or {}, []
+    if "persistent" in modes:
+        tiles, r = api.batch_tune(ents, objective, mo, start=tiles or None)
+        recs += r
+    if "launches" in modes:
+        tiles, r = api.batch_tune_launches(ents, objective, mo, start=tiles or None)
+        recs += r
     log(json.dumps(dict(batched_tiles=api.tiles_to_json(tiles), points=len(recs),
                         wall_s=time.time() - t0)))
     if out:
@@ -123,9 +131,11 @@ def main():
     ap.add_argument("--cache", default=None)
     ap.add_argument("--out", default=os.path.join(HERE, "tuned_configs.json"))
     ap.add_argument("--records", default=None, help="write every record (JSON lines)")
+    ap.add_argument("--batch-modes", default="persistent,launches",
+                    help="batched256: which tables to tune (persistent, launches)")
     a = ap.parse_args()
     if a.workload == "batched256":
-        tune_batched(a.objective, a.window, a.out)
+        tune_batched(a.objective, a.window, a.out, modes=tuple(a.batch_modes.split(",")))
         return
     summary, recs = run(a.workload, a.space, a.objective, a.window, a.prefilter, a.cache, a.out)
     if a.records:

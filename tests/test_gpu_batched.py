@@ -134,6 +134,34 @@ def test_bucket_tuning_and_measurement():
         assert max_rel_err(o.cpu().numpy()[:, :p.out_w], oracle_ref(p)) <= MAX_REL
 
 
+def test_launches_tuning():
+    probs = synth.batch_problems(20, seed=9, lo=64, hi=700)
+    probs.append(synth.conv_problem(90, 77, 5, seed=[9, 99], pitch_align=1))  # no TMA
+    ents, outs = device_entries(probs)
+    start = {(0, 5): (64, 2), ("claim", 0): 2}
+    tiles, recs = api.batch_tune_launches(ents, "energy",
+                                          api.measure_options(window_s=0.1, warmup_s=0.05),
+                                          start=start)
+    ks = {(int(p.out_h * p.out_w >= 512 * 512), p.fh) for p in probs}
+    assert {key for key in tiles if key[0] in ("L0", "L1")} == {(f"L{c}", k) for c, k in ks}
+    assert tiles[(0, 5)] == (64, 2) and tiles[("claim", 0)] == 2  # other entries kept
+    assert len(recs) == 9 * len(ks)
+    for key, val in tiles.items():
+        if key[0] in ("L0", "L1"):
+            assert tuple(val) in {(16, 8, 4), (32, 4, 4), (32, 2, 4), (16, 4, 4), (64, 2, 4),
+                                    (32, 8, 2), (32, 4, 2), (64, 4, 2), (128, 2, 2)}
+    ents_p, outs_p = device_entries(probs)
+    with api.Batch(ents, tiles, mode="launches") as b, api.Batch(ents_p, tiles) as bp:
+        b.run()
+        bp.run_plain()
+        torch.cuda.synchronize()
+    for p, o, op in zip(probs, outs, outs_p):
+        a = o.cpu().numpy()[:, :p.out_w]
+        assert np.array_equal(a, op.cpu().numpy()[:, :p.out_w])
+        assert max_rel_err(a, oracle_ref(p)) <= MAX_REL
+    assert api.status_read(clear=True) == 0
+
+
 def test_many_images_fill_every_parameter_block_then_fall_back():
     # 6000 one-output 17x17 images: their taps fill a parameter block every
     # 23 images, so the launches run out (254 per batch) and the last images
