@@ -96,3 +96,19 @@ def test_explicit_band_split_is_checked_on_the_host(lib):
                                             ctypes.byref(c), arr, len(rows), None)
     for bad in ([8, 0], [4, 3], [4, 5], [1] * 65, [-1, 9]):
         assert run(bad) == api.CT_EINVAL, bad
+
+
+def test_batch_modes_host_checks_and_tiles_round_trip(lib):
+    # null handles are refused before any device work
+    assert lib.ct_batch_run_mode(None, api.BATCH_RUNS["launches"], None) == api.CT_EINVAL
+    assert lib.ct_batch_run(None, None) == api.CT_EINVAL
+    assert lib.ct_measure_batch(None, 0, None, None, None) == api.CT_EINVAL
+    n = ctypes.c_int(0)
+    assert lib.ct_batch_tune_launches(None, 0, 0, None, None, None, None, 0,
+                                      ctypes.byref(n)) == api.CT_EINVAL
+    # every kind of tiles entry survives the struct and the JSON form
+    tiles = {(0, 3): (16, 8), (1, 17): (32, 4), ("threads", 1): 128, ("claim", 0): 2,
+             ("L0", 5): (32, 4, 2), ("L1", 17): (16, 8, 4), ("mode", 0): api.BATCH_MODES["launches"]}
+    assert api.CtBatchTiles.from_dict(tiles).to_dict() == tiles
+    assert api.tiles_from_json(api.tiles_to_json(tiles)) == tiles
+    assert ctypes.sizeof(api.CtBatchTiles) == 4 * (2 * 18 * 5 + 3 + 3 + 1)
