@@ -576,7 +576,7 @@ int launch_config(const ct_batch_item& it, const float* taps, const ct_batch_til
 }
 
 // The launches graph's work: fork `s` to the branches, one single-image
-// launch per image (largest work first) on branch n % branches, join.
+// launch per image (in the order above) on branch n % branches, join.
 int enqueue_launches(ct_batch* b, cudaStream_t s) {
   const int nb = (int)b->lbranches.size();
   if (nb == 0) return CT_ENOTSUP;
@@ -671,14 +671,17 @@ int build_batch(const ct_batch_item* items, int n, const ct_batch_tiles* tiles, 
     return cuda_status(e);
   if ((e = cudaMalloc(&b->d_counter, kBatchCounterBytes)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemset(b->d_counter, 0, kBatchCounterBytes)) != cudaSuccess) return cuda_status(e);
-  // launches mode: every image's problem and configuration, largest work
-  // first (stable: equal work keeps input order)
+  // launches mode: every image's problem and configuration, by filter side
+  // (largest first), then by output area (largest first; stable: ties keep
+  // input order).  Round-robin over the branches, the kernels running side
+  // by side then mostly share one filter side's code in the instruction
+  // caches (GB300, 256-image batch: 877-883 us, against 977-984 us with the
+  // images ordered by work alone, sides mixed).
   if (b->host_images.size() <= (size_t)CT_BATCH_LAUNCH_MAX_IMAGES) {
     std::vector<int> by_work(b->order);
     std::stable_sort(by_work.begin(), by_work.end(), [&](int x, int y) {
-      const double wx = (double)items[x].k * items[x].k * items[x].out_h * items[x].out_w;
-      const double wy = (double)items[y].k * items[y].k * items[y].out_h * items[y].out_w;
-      return wx > wy;
+      if (items[x].k != items[y].k) return items[x].k > items[y].k;
+      return (double)items[x].out_h * items[x].out_w > (double)items[y].out_h * items[y].out_w;
     });
     for (int i : by_work) {
       ct_problem p;
