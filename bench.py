@@ -18,7 +18,7 @@ At N = 1 the same line also carries, each with its own SM-clock record:
                                       L2 flushed, against min(FP32, AI x HBM);
   batched256                          the 256-image batch as one CUDA-graph
                                       launch (the batch's mode: one single-
-                                      image kernel per image over 16 graph
+                                      image kernel per image over 12 graph
                                       branches), the persistent class kernels'
                                       graph, and one host-issued plain launch
                                       per image (GFLOP/s, GFLOP/J, mixed

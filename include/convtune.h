@@ -565,7 +565,7 @@ int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
  *    (0 or invalid entries: 32 x 8 threads, tile_y 2).
  *  - launches: one single-image kernel per image (compile-time filter side,
  *    taps in its parameter block), ordered by filter side and then output
- *    area (largest first), round-robin over 16 parallel graph branches; per bucket block_x x block_y threads and
+ *    area (largest first), round-robin over 12 parallel graph branches; per bucket block_x x block_y threads and
  *    tile_y from the launch_* fields of ct_batch_tiles (0: 16 x 8, tile_y 4),
  *    TMA staging where the input allows it.  Captured for batches of at most
  *    CT_BATCH_LAUNCH_MAX_IMAGES images, unless the mode asked for is

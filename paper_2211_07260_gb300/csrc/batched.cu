@@ -264,9 +264,10 @@ const void* batched_kernel_fn(int cls) {
 namespace {
 
 constexpr size_t kBatchBranches = 8;  // parallel branches of a captured batch graph
-// Parallel branches of the launches graph (GB300, 256-image batch, one
-// single-image launch per image: 16 branches 979 us, 8 branches 1008 us).
-constexpr size_t kBatchLaunchBranches = 16;
+// Parallel branches of the launches graph (GB300, 256-image batch ordered
+// by filter side: 8, 10 and 12 branches 856-857 us, 16 branches 878-885 us,
+// 24 branches 890-893 us).
+constexpr size_t kBatchLaunchBranches = 12;
 // Launches-mode candidates of the per-bucket tuner: (block_x, block_y,
 // tile_y), 128 or 256 threads and 4-wide tiles, as in the single-image
 // kernel's fastest configurations (4096^2 / 17 x 17 and 1024^2 / 7 x 7).
