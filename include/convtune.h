@@ -569,7 +569,9 @@ int ct_tune_steered(const ct_problem* p, const ct_config* space, int n_space,
  *    tile_y from the launch_* fields of ct_batch_tiles (0: 16 x 8, tile_y 4),
  *    TMA staging where the input allows it.  Captured for batches of at most
  *    CT_BATCH_LAUNCH_MAX_IMAGES images, unless the mode asked for is
- *    CT_BATCH_PERSISTENT.
+ *    CT_BATCH_PERSISTENT; ct_batch_create then runs these launches once
+ *    (writing every output, and returning after they finish) before it
+ *    captures them, so that kernels are loaded outside the capture.
  *
  * ct_batch_run replays the batch's mode: ct_batch_tiles.mode, where
  * CT_BATCH_AUTO takes the launches graph when it exists and the images
