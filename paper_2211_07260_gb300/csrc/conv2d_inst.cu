@@ -25,6 +25,8 @@ const void* pick_tile(bool staged, bool filt_smem, bool big_cta) {
     if (filt_smem) return (const void*)conv2d_kernel<K, TX, TY, true, true>;
     if constexpr (uses_ring(K, TX, TY))
       if (big_cta) return (const void*)conv2d_kernel<K, TX, TY, true, false, true>;
+    if constexpr (K == 17 && TX == 4 && TY == 4)
+      return (const void*)conv2d_kernel_r96<K, TX, TY, true, false>;
     return (const void*)conv2d_kernel<K, TX, TY, true, false>;
   }
   return filt_smem ? (const void*)conv2d_kernel<K, TX, TY, false, true>

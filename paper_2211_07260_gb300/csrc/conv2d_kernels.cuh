@@ -498,7 +498,7 @@ __device__ __forceinline__ void accumulate_tile_ring(float (&acc)[TY][TX], RowPt
 //                        [staged tile tile_h x smem_pitch (if STAGED)]
 // ----------------------------------------------------------------------------
 template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM, bool REM_FIRST = false>
-__global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K)> a) {
+__device__ __forceinline__ void conv2d_body(const ConvArgs<K * tap_row_pad(K)>& a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // tap rows padded to a multiple of 4 floats (in the parameters and in
   // shared memory): 4 taps per 16-byte load
@@ -637,6 +637,24 @@ __global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K
       if (y < a.out_h) store_run<TX>(a.out + (long long)y * a.out_pitch, x0, a.out_w, a.vw, acc[t]);
     }
   }
+}
+
+template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM, bool REM_FIRST = false>
+__global__ void conv2d_kernel(const __grid_constant__ ConvArgs<K * tap_row_pad(K)> a) {
+  conv2d_body<K, TX, TY, STAGED, FILT_SMEM, REM_FIRST>(a);
+}
+
+// The same variant held to 96 registers.  Used for the 17 x 17 body with
+// 4 x 4 tiles, staged, taps in the parameter space and the left-over filter
+// rows last (CTAs of up to 4 warps): five CTAs of 128 threads then fit on an
+// SM instead of four (108 registers uncapped, 28 bytes spilled capped; GB300,
+// 4096^2: 150.8 -> 146.0 us per launch at 16 x 8 threads, 150.1 -> 145.6 us
+// at 32 x 4, 32 x 1 unchanged).  Same instructions per output, so the same
+// bits.
+template <int K, int TX, int TY, bool STAGED, bool FILT_SMEM, bool REM_FIRST = false>
+__global__ void __maxnreg__(96)
+    conv2d_kernel_r96(const __grid_constant__ ConvArgs<K * tap_row_pad(K)> a) {
+  conv2d_body<K, TX, TY, STAGED, FILT_SMEM, REM_FIRST>(a);
 }
 
 }  // namespace convtune
