@@ -284,6 +284,10 @@ def timed_steps(world, stream, steps, launch, flush=None):
     barrier(world)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
+        # ~1 ms of device sleep before the first step (outside every step's
+        # events): the host enqueues ahead of the device, so no host-side
+        # submission latency of the first launch falls inside its span
+        torch.cuda._sleep(2_000_000)
         for s, e in ev:
             if flush is not None:
                 flush.zero_()
@@ -567,6 +571,9 @@ def main():
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
+        # device sleep before the first step (outside every step's events),
+        # as in timed_steps: the host enqueues ahead of the device
+        torch.cuda._sleep(2_000_000)
         for s, e in ev:
             flush.zero_()          # L2 flush, outside the timed span
             s.record(stream)
@@ -577,6 +584,9 @@ def main():
     wall = time.perf_counter() - wall0
     step_ms = [s.elapsed_time(e) for s, e in ev]
     kernel_s = all_max(world, sum(step_ms) / 1e3)
+    srt = sorted(step_ms)
+    step_stats = dict(min_us=srt[0] * 1e3, median_us=srt[len(srt) // 2] * 1e3,
+                      max_us=srt[-1] * 1e3, first_us=step_ms[0] * 1e3)
     # the time-optimal configuration of the same sweep, timed the same way
     time_tuned = None
     te = None if args.config else tuned_entry(info["name"], wl)
@@ -640,6 +650,7 @@ def main():
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": kernel_s * 1e3 / args.steps,
+        "step_us": step_stats,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
