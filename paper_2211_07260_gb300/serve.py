@@ -118,7 +118,9 @@ def main():
     ap.add_argument("--max-requests", type=int, default=20000)
     ap.add_argument("--payloads", type=int, default=256)
     ap.add_argument("--modes", default="batched,plain")
-    ap.add_argument("--tiles", default=None, help="JSON file of per-bucket tiles")
+    ap.add_argument("--tiles", default=None,
+                    help="JSON file of per-bucket tiles, or a tuned-configuration table "
+                         "(its batched_tiles entry for this device)")
     ap.add_argument("--out", default=None)
     ap.add_argument("--trace", type=int, default=0,
                     help="keep a timeline of the last N batches and report the slowest")
@@ -126,6 +128,8 @@ def main():
     tiles = None
     if a.tiles:
         raw = json.load(open(a.tiles))
+        if "batched_tiles" in raw:  # a tuned-configuration table
+            raw = raw["batched_tiles"].get(api.device_info()["name"], {})
         tiles = api.tiles_from_json(raw)
     payloads = make_payloads(a.payloads)
     p_idle = idle_power()
