@@ -468,7 +468,7 @@ struct ct_batch {
   // so that one launch's last tiles overlap the next launch's first ones
   std::vector<cudaStream_t> branches;
   std::vector<cudaEvent_t> events;  // one per branch + the fork
-  // launches graph: one single-image kernel per image, largest work first
+  // launches graph: one single-image kernel per image, by filter side, then area
   std::vector<ct_problem> lprob;
   std::vector<ct_config> lcfg;
   cudaGraphExec_t exec_launch = nullptr;
