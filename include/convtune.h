@@ -140,6 +140,29 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
                        const ct_config* c, void* stream);
 
 /*
+ * ct_conv2d_run_host that returns once the work is enqueued: the copies in,
+ * the kernels and the copies out run on library streams, ordered after the
+ * earlier host-buffer calls of this device (not after any caller stream:
+ * `in` must hold its data at the call).  ct_conv2d_host_wait returns when
+ * every earlier call's output is in its `out`; until then `in` must stay
+ * allocated and unmodified and `out` allocated and unread.  The taps are
+ * taken at the call.  The library keeps two sets of device buffers and
+ * alternates them between calls, so a call's copies in overlap the previous
+ * call's kernels and copies out (a stream of images keeps the host link
+ * busy in both directions); each call is split into two row bands (one
+ * below 512 rows).  With pageable host memory the copies may block
+ * the calling thread.  Same arguments and errors as ct_conv2d_run_host;
+ * errors found while enqueueing wait for the library's streams before
+ * returning.  (Not in the paper: host-side pipelining.)
+ */
+int ct_conv2d_run_host_async(const float* in_host, long in_pitch, const float* filt, int fh,
+                             int fw, float* out_host, long out_pitch, int out_h, int out_w,
+                             const ct_config* c);
+/* Wait for every earlier ct_conv2d_run_host_async call of the current
+   device; returns the first CUDA error seen by them (CT_ECUDA) or CT_OK. */
+int ct_conv2d_host_wait(void);
+
+/*
  * ct_conv2d_run_host with the row bands given by the caller: band b covers
  * band_rows[b] output rows, in order from row 0 (band_rows[b] >= 1, their sum
  * == out_h, 1 <= n_bands <= 64; otherwise CT_EINVAL).  Each band is one

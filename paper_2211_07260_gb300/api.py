@@ -186,6 +186,9 @@ _SIGS = {
     "ct_conv2d_run": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ct_conv2d_run_host": (c_int, [c_void_p, c_long, c_void_p, c_int, c_int, c_void_p, c_long,
                                    c_int, c_int, c_void_p, c_void_p]),
+    "ct_conv2d_run_host_async": (c_int, [c_void_p, c_long, c_void_p, c_int, c_int, c_void_p,
+                                         c_long, c_int, c_int, c_void_p]),
+    "ct_conv2d_host_wait": (c_int, []),
     "ct_conv2d_run_host_bands": (c_int, [c_void_p, c_long, c_void_p, c_int, c_int, c_void_p, c_long,
                                          c_int, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     "ct_conv2d_host_bands_default": (c_int, [c_int, c_void_p, c_int, c_void_p]),
@@ -376,6 +379,29 @@ def conv2d_run_host(inp: np.ndarray, filt, out: np.ndarray, out_h: int, out_w: i
     _check(lib().ct_conv2d_run_host_bands(*args, rows.ctypes.data, int(rows.size),
                                           c_void_p(stream_handle(stream))),
            "ct_conv2d_run_host_bands")
+
+
+def conv2d_run_host_async(inp: np.ndarray, filt, out: np.ndarray, out_h: int, out_w: int,
+                          cfg: Config):
+    """ct_conv2d_run_host_async: enqueue the host-buffer correlation (after
+    the earlier host-buffer calls) and return.  Keep `inp` and `out` alive,
+    `inp` unmodified and `out` unread, until host_wait() returns."""
+    if inp.dtype != np.float32 or out.dtype != np.float32:
+        raise TypeError("float32 arrays required")
+    if not (inp.flags.c_contiguous and out.flags.c_contiguous):
+        raise ValueError("contiguous arrays required")
+    f = _taps(filt)
+    c = cfg.to_c()
+    _check(lib().ct_conv2d_run_host_async(inp.ctypes.data, inp.shape[1], f.ctypes.data,
+                                          f.shape[0], f.shape[1], out.ctypes.data, out.shape[1],
+                                          int(out_h), int(out_w), ctypes.byref(c)),
+           "ct_conv2d_run_host_async")
+
+
+def host_wait():
+    """ct_conv2d_host_wait: every earlier conv2d_run_host_async output is on
+    the host when this returns."""
+    _check(lib().ct_conv2d_host_wait(), "ct_conv2d_host_wait")
 
 
 def host_bands_default(out_h: int) -> list:

@@ -27,14 +27,19 @@ struct DeviceState {
   int smem_optin = 0;
   int sm_count = 0;
   std::set<const void*> smem_raised;  // kernels whose dynamic shared-memory cap is raised
-  // buffers of the host-buffer entry point
-  float* din = nullptr;
-  size_t din_bytes = 0;
-  float* dout = nullptr;
-  size_t dout_bytes = 0;
+  // buffers of the host-buffer entry point: two sets, used by alternate
+  // calls, so that a call's copies in overlap the previous call's kernels
+  // and copies out
+  float* din[2] = {nullptr, nullptr};
+  size_t din_bytes[2] = {0, 0};
+  float* dout[2] = {nullptr, nullptr};
+  size_t dout_bytes[2] = {0, 0};
+  int host_slot = 0;  // the set the next call uses
   // streams and events of the pipelined host-buffer entry point
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
-  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_slot_k[2] = {nullptr, nullptr};    // last kernel of the set's last call
+  cudaEvent_t ev_slot_out[2] = {nullptr, nullptr};  // last copy out of the set's last call
   std::vector<cudaEvent_t> ev_in, ev_k;
 };
 
@@ -438,9 +443,14 @@ std::vector<int> default_host_bands(int out_h) {
   return rows;
 }
 
+// One host-buffer call over the given row bands.  sync: start after the
+// caller's earlier work on `stream`, make `stream` wait for the last copy
+// out and return when the output is in out_host.  Otherwise: return once
+// everything is enqueued, ordered only after the earlier host-buffer calls
+// (ct_conv2d_host_wait waits for it).
 int run_host_bands(const float* in_host, long in_pitch, const float* filt, int fh, int fw,
                    float* out_host, long out_pitch, int out_h, int out_w, const ct_config* c,
-                   const int* band_rows, int n_bands, void* stream) {
+                   const int* band_rows, int n_bands, void* stream, bool sync) {
   std::lock_guard<std::mutex> lk(g_host_mu);
   int err = CT_OK;
   DeviceState* st = current_state(nullptr, &err);
@@ -451,26 +461,19 @@ int run_host_bands(const float* in_host, long in_pitch, const float* filt, int f
   const size_t in_bytes = in_row * (size_t)in_h;
   const size_t out_bytes = out_row * (size_t)out_h;
   cudaError_t e;
-  if (st->din_bytes < in_bytes) {
-    if (st->din) cudaFree(st->din);
-    st->din = nullptr;
-    st->din_bytes = 0;
-    if ((e = cudaMalloc(&st->din, in_bytes)) != cudaSuccess) return cuda_status(e);
-    st->din_bytes = in_bytes;
-  }
-  if (st->dout_bytes < out_bytes) {
-    if (st->dout) cudaFree(st->dout);
-    st->dout = nullptr;
-    st->dout_bytes = 0;
-    if ((e = cudaMalloc(&st->dout, out_bytes)) != cudaSuccess) return cuda_status(e);
-    st->dout_bytes = out_bytes;
-  }
   if (!st->s_in) {
     if ((e = cudaStreamCreateWithFlags(&st->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&st->s_comp, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&st->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&st->ev_start, cudaEventDisableTiming)) != cudaSuccess)
+        (e = cudaEventCreateWithFlags(&st->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&st->ev_end, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_status(e);
+    for (int q = 0; q < 2; ++q)
+      if ((e = cudaEventCreateWithFlags(&st->ev_slot_k[q], cudaEventDisableTiming)) !=
+              cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&st->ev_slot_out[q], cudaEventDisableTiming)) !=
+              cudaSuccess)
+        return cuda_status(e);
     st->ev_in.resize(kHostMaxBands);
     st->ev_k.resize(kHostMaxBands);
     for (int b = 0; b < kHostMaxBands; ++b)
@@ -478,12 +481,40 @@ int run_host_bands(const float* in_host, long in_pitch, const float* filt, int f
           (e = cudaEventCreateWithFlags(&st->ev_k[b], cudaEventDisableTiming)) != cudaSuccess)
         return cuda_status(e);
   }
+  const int slot = st->host_slot;
+  if (st->din_bytes[slot] < in_bytes || st->dout_bytes[slot] < out_bytes) {
+    // the set may still be in use by an earlier asynchronous call
+    if ((e = cudaStreamSynchronize(st->s_in)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st->s_comp)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st->s_out)) != cudaSuccess)
+      return cuda_status(e);
+    if (st->din_bytes[slot] < in_bytes) {
+      if (st->din[slot]) cudaFree(st->din[slot]);
+      st->din[slot] = nullptr;
+      st->din_bytes[slot] = 0;
+      if ((e = cudaMalloc(&st->din[slot], in_bytes)) != cudaSuccess) return cuda_status(e);
+      st->din_bytes[slot] = in_bytes;
+    }
+    if (st->dout_bytes[slot] < out_bytes) {
+      if (st->dout[slot]) cudaFree(st->dout[slot]);
+      st->dout[slot] = nullptr;
+      st->dout_bytes[slot] = 0;
+      if ((e = cudaMalloc(&st->dout[slot], out_bytes)) != cudaSuccess) return cuda_status(e);
+      st->dout_bytes[slot] = out_bytes;
+    }
+  }
+  st->host_slot ^= 1;
+  float* const din = st->din[slot];
+  float* const dout = st->dout[slot];
   // The input rows of band b travel in while band b-1 computes and band
   // b-2's outputs travel back (host <-> device copies run both ways at
   // once).  Input chunk b holds only the rows band b needs beyond the earlier
   // chunks; each output is computed exactly as in one launch.  (One stream
   // per stage: spreading the bands over two streams per stage, so that two
-  // copies of one direction run at once, measured slower.)
+  // copies of one direction run at once, measured slower.)  Across calls
+  // the two buffer sets alternate: this call's copies in wait only for the
+  // kernels of the call before last (which read the same input buffer), its
+  // kernels for that call's copies out (which read the same output buffer).
   int rc = CT_OK;
   auto fail = [&](int code) {
     cudaStreamSynchronize(st->s_in);
@@ -492,15 +523,18 @@ int run_host_bands(const float* in_host, long in_pitch, const float* filt, int f
     return code;
   };
   // start after the caller's earlier work on `stream`
-  if ((e = cudaEventRecord(st->ev_start, (cudaStream_t)stream)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(st->s_in, st->ev_start, 0)) != cudaSuccess)
+  if (sync && ((e = cudaEventRecord(st->ev_start, (cudaStream_t)stream)) != cudaSuccess ||
+               (e = cudaStreamWaitEvent(st->s_in, st->ev_start, 0)) != cudaSuccess))
+    return fail(cuda_status(e));
+  if ((e = cudaStreamWaitEvent(st->s_in, st->ev_slot_k[slot], 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st->s_comp, st->ev_slot_out[slot], 0)) != cudaSuccess)
     return fail(cuda_status(e));
   int in_done = 0;  // input rows already sent
   int y0 = 0;
   for (int b = 0; b < n_bands; ++b) {
     const int rb = band_rows[b];
     const int need = y0 + rb + fh - 1;  // input rows band b reads (> in_done: rb >= 1)
-    e = cudaMemcpyAsync(reinterpret_cast<char*>(st->din) + in_row * in_done,
+    e = cudaMemcpyAsync(reinterpret_cast<char*>(din) + in_row * in_done,
                         reinterpret_cast<const char*>(in_host) + in_row * in_done,
                         in_row * (size_t)(need - in_done), cudaMemcpyHostToDevice, st->s_in);
     if (e != cudaSuccess) return fail(cuda_status(e));
@@ -509,12 +543,12 @@ int run_host_bands(const float* in_host, long in_pitch, const float* filt, int f
         (e = cudaStreamWaitEvent(st->s_comp, st->ev_in[b], 0)) != cudaSuccess)
       return fail(cuda_status(e));
     ct_problem p;
-    p.in = st->din + (size_t)y0 * in_pitch;
+    p.in = din + (size_t)y0 * in_pitch;
     p.in_pitch = in_pitch;
     p.filt = filt;
     p.fh = fh;
     p.fw = fw;
-    p.out = st->dout + (size_t)y0 * out_pitch;
+    p.out = dout + (size_t)y0 * out_pitch;
     p.out_pitch = out_pitch;
     p.out_h = rb;
     p.out_w = out_w;
@@ -525,16 +559,23 @@ int run_host_bands(const float* in_host, long in_pitch, const float* filt, int f
     // the caller's padding columns (out_w .. out_pitch) are left untouched
     if (out_pitch == out_w)
       e = cudaMemcpyAsync(reinterpret_cast<char*>(out_host) + out_row * y0,
-                          reinterpret_cast<const char*>(st->dout) + out_row * y0,
+                          reinterpret_cast<const char*>(dout) + out_row * y0,
                           out_row * (size_t)rb, cudaMemcpyDeviceToHost, st->s_out);
     else
       e = cudaMemcpy2DAsync(reinterpret_cast<char*>(out_host) + out_row * y0, out_row,
-                            reinterpret_cast<const char*>(st->dout) + out_row * y0, out_row,
+                            reinterpret_cast<const char*>(dout) + out_row * y0, out_row,
                             sizeof(float) * (size_t)out_w, rb, cudaMemcpyDeviceToHost,
                             st->s_out);
     if (e != cudaSuccess) return fail(cuda_status(e));
     y0 += rb;
   }
+  if ((e = cudaEventRecord(st->ev_slot_k[slot], st->s_comp)) != cudaSuccess ||
+      (e = cudaEventRecord(st->ev_slot_out[slot], st->s_out)) != cudaSuccess)
+    return fail(cuda_status(e));
+  if (!sync) return CT_OK;
+  if ((e = cudaEventRecord(st->ev_end, st->s_out)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent((cudaStream_t)stream, st->ev_end, 0)) != cudaSuccess)
+    return fail(cuda_status(e));
   return cuda_status(cudaStreamSynchronize(st->s_out));
 }
 
@@ -559,7 +600,32 @@ int ct_conv2d_run_host(const float* in_host, long in_pitch, const float* filt, i
   if (rc != CT_OK || out_h == 0 || out_w == 0) return rc;
   const std::vector<int> rows = default_host_bands(out_h);
   return run_host_bands(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c,
-                        rows.data(), (int)rows.size(), stream);
+                        rows.data(), (int)rows.size(), stream, true);
+}
+
+int ct_conv2d_run_host_async(const float* in_host, long in_pitch, const float* filt, int fh,
+                             int fw, float* out_host, long out_pitch, int out_h, int out_w,
+                             const ct_config* c) {
+  int rc = host_args_check(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c);
+  if (rc != CT_OK || out_h == 0 || out_w == 0) return rc;
+  // two row bands (one below 512 rows): back-to-back calls overlap one
+  // another, so fewer, larger copies than the synchronous split are best
+  // (GB300, 4096^2 / 17 x 17, calls back to back: 1 band 0.471 ms per call,
+  // 2 bands 0.427, 4 bands 0.492, 8 bands 0.517)
+  std::vector<int> rows;
+  if (out_h >= 512) rows = {out_h - out_h / 2, out_h / 2};
+  else rows = {out_h};
+  return run_host_bands(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c,
+                        rows.data(), (int)rows.size(), nullptr, false);
+}
+
+int ct_conv2d_host_wait(void) {
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  int err = CT_OK;
+  DeviceState* st = current_state(nullptr, &err);
+  if (!st) return err;
+  if (!st->s_out) return CT_OK;  // no host-buffer call yet
+  return cuda_status(cudaStreamSynchronize(st->s_out));
 }
 
 int ct_conv2d_run_host_bands(const float* in_host, long in_pitch, const float* filt, int fh,
@@ -577,7 +643,7 @@ int ct_conv2d_run_host_bands(const float* in_host, long in_pitch, const float* f
   if (total != out_h) return CT_EINVAL;
   if (out_w == 0) return CT_OK;
   return run_host_bands(in_host, in_pitch, filt, fh, fw, out_host, out_pitch, out_h, out_w, c,
-                        band_rows, n_bands, stream);
+                        band_rows, n_bands, stream, true);
 }
 
 int ct_conv2d_host_bands_default(int out_h, int* band_rows, int cap, int* n_bands) {

@@ -256,20 +256,63 @@ def test_host_entry_point_repeated_calls(pinned):
     assert max_rel_err(out, oracle_ref(prob)) <= MAX_REL
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_point_asynchronous_calls(pinned):
+    # back-to-back asynchronous calls, each with its own input and output
+    # (the library alternates two device buffer sets); the third
+    # call is larger, so its buffer set is reallocated while the second call
+    # may still run.  Every output equals the synchronous entry point's.
+    cfg = api.Config(32, 4, 4, 2, api.STAGE_TMA, api.FILTER_CONST, 4)
+    shapes = [(1100, 300, 7), (900, 260, 7), (1500, 400, 7), (1100, 300, 7), (300, 200, 5)]
+    probs = [synth.conv_problem(h, w, k, seed=[31, i]) for i, (h, w, k) in enumerate(shapes)]
+    ins, outs = [], []
+    for p in probs:
+        a = np.ascontiguousarray(p.inp)
+        o = np.full((p.out_h, p.out_w), -1.0, np.float32)
+        if pinned:
+            a = torch.from_numpy(a).pin_memory().numpy()
+            o = torch.from_numpy(o).pin_memory().numpy()
+        ins.append(a)
+        outs.append(o)
+    for p, a, o in zip(probs, ins, outs):
+        api.conv2d_run_host_async(a, p.filt, o, p.out_h, p.out_w, cfg)
+    api.host_wait()
+    for p, o in zip(probs, outs):
+        ref = np.empty((p.out_h, p.out_w), np.float32)
+        api.conv2d_run_host(p.inp, p.filt, ref, p.out_h, p.out_w, cfg)
+        assert np.array_equal(o, ref)
+        assert max_rel_err(o, oracle_ref(p)) <= MAX_REL
+    # a synchronous call after an asynchronous one runs after it, and
+    # returns with both outputs on the host
+    (p0, a0, o0), (p1, a1, o1) = zip(probs[:2], ins[:2], outs[:2])
+    o0.fill(-1.0)
+    o1.fill(-1.0)
+    api.conv2d_run_host_async(a0, p0.filt, o0, p0.out_h, p0.out_w, cfg)
+    api.conv2d_run_host(a1, p1.filt, o1, p1.out_h, p1.out_w, cfg)
+    assert max_rel_err(o0, oracle_ref(p0)) <= MAX_REL
+    assert max_rel_err(o1, oracle_ref(p1)) <= MAX_REL
+    api.host_wait()
+    assert api.status_read(clear=True) == 0
+
+
 @pytest.mark.parametrize("which", ["1024x1024_k7", "4096x4096_k17"])
 def test_full_size_workloads(which):
     # the tuned configurations the bench times (energy- and time-optimal),
     # then others of the space; all must give the same bits
     if which == "1024x1024_k7":
         prob = synth.conv_problem(1024, 1024, 7, seed=0)
-        cfgs = [api.Config(64, 8, 4, 4, api.STAGE_SMEM, api.FILTER_CONST, 4),
+        cfgs = [api.Config(128, 4, 4, 4, api.STAGE_SMEM, api.FILTER_CONST, 4),
+                api.Config(32, 4, 4, 2, api.STAGE_SMEM, api.FILTER_CONST, 4),
+                api.Config(64, 8, 4, 4, api.STAGE_SMEM, api.FILTER_CONST, 4),
                 api.Config(32, 8, 4, 4, api.STAGE_SMEM, api.FILTER_CONST, 4),
                 api.Config(32, 4, 4, 4, api.STAGE_SMEM, api.FILTER_CONST, 4),
                 api.Config(64, 2, 2, 2, api.STAGE_DIRECT, api.FILTER_CONST, 2),
                 api.Config(128, 4, 4, 4, api.STAGE_TMA, api.FILTER_CONST, 4)]
     else:
         prob = synth.conv_problem(4096, 4096, 17, seed=1)
-        cfgs = [api.Config(32, 4, 4, 4, api.STAGE_TMA, api.FILTER_CONST, 4),
+        cfgs = [api.Config(128, 8, 4, 2, api.STAGE_TMA, api.FILTER_CONST, 4),
+                api.Config(32, 4, 4, 4, api.STAGE_TMA, api.FILTER_CONST, 4),  # 96 registers
+                api.Config(16, 8, 4, 4, api.STAGE_TMA, api.FILTER_CONST, 4),  # 96 registers
                 api.Config(32, 1, 4, 4, api.STAGE_TMA, api.FILTER_CONST, 4),
                 api.Config(32, 8, 4, 4, api.STAGE_SMEM, api.FILTER_CONST, 4),
                 api.Config(64, 2, 4, 4, api.STAGE_TMA, api.FILTER_CONST, 4)]
