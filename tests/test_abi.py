@@ -98,6 +98,20 @@ def test_explicit_band_split_is_checked_on_the_host(lib):
         assert run(bad) == api.CT_EINVAL, bad
 
 
+def test_async_host_entry_checks_arguments_on_the_host(lib):
+    taps = (ctypes.c_float * 9)()
+    buf_in = (ctypes.c_float * (10 * 10))()
+    buf_out = (ctypes.c_float * (8 * 8))()
+    c = api.Config().to_c()
+    run = lib.ct_conv2d_run_host_async
+    assert run(buf_in, 10, None, 3, 3, buf_out, 8, 8, 8, ctypes.byref(c)) == api.CT_EINVAL
+    assert run(None, 10, taps, 3, 3, buf_out, 8, 8, 8, ctypes.byref(c)) == api.CT_EINVAL
+    assert run(buf_in, 9, taps, 3, 3, buf_out, 8, 8, 8, ctypes.byref(c)) == api.CT_EINVAL  # pitch
+    assert run(buf_in, 10, taps, 3, 3, buf_out, 8, 8, 8, None) == api.CT_EINVAL
+    # nothing to do: no device work, no error
+    assert run(buf_in, 10, taps, 3, 3, buf_out, 8, 0, 8, ctypes.byref(c)) == api.CT_OK
+
+
 def test_batch_modes_host_checks_and_tiles_round_trip(lib):
     # null handles are refused before any device work
     assert lib.ct_batch_run_mode(None, api.BATCH_RUNS["launches"], None) == api.CT_EINVAL
