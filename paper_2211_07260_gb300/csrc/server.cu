@@ -206,11 +206,11 @@ int ct_server::dispatch(Slot& sl, std::vector<Request*>& batch) {
       if ((rc = ct_conv2d_run(&p, &c, sl.s)) != CT_OK) return rc;
     }
   } else {
-    // the table runs in filter-side class order (one persistent kernel per
-    // class); the caller's order of `batch` does not matter beyond this
-    std::stable_sort(batch.begin(), batch.end(), [](const Request* x, const Request* y) {
-      return batch_class_of(x->k) < batch_class_of(y->k);
-    });
+    // the table runs in filter-side order (so in class order too: one
+    // persistent kernel per class, whose CTAs then take one side's items in
+    // a row); the caller's order of `batch` does not matter beyond this
+    std::stable_sort(batch.begin(), batch.end(),
+                     [](const Request* x, const Request* y) { return x->k < y->k; });
     const double t_plan0 = now_s();
     long long first = 0;
     for (size_t q = 0; q < batch.size(); ++q) {
