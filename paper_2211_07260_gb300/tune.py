@@ -8,8 +8,8 @@ workload at default clocks and record the chosen configuration.
 then measures energy only for the N fastest points; without it every point
 gets an energy window.  Results are cached (JSON lines) so a sweep resumes.
 
---confirm C --repeats R re-measures the C best points of the objective R
-more times, the C points one after the other in each round (so that slow
+--confirm C --repeats R (default 8 and 4; --confirm 0 turns it off)
+re-measures the C best points of the objective R more times, the C points one after the other in each round (so that slow
 drifts of power or temperature reach all of them alike), and keeps the point
 with the best median: near-ties among the top points (GB300, 4096^2 / 17 x
 17: the three most energy-efficient within 0.14 %, below one window's
@@ -181,9 +181,9 @@ def main():
     ap.add_argument("--cache", default=None)
     ap.add_argument("--out", default=os.path.join(HERE, "tuned_configs.json"))
     ap.add_argument("--records", default=None, help="write every record (JSON lines)")
-    ap.add_argument("--confirm", type=int, default=0,
-                    help="re-measure this many of the best points (with --repeats)")
-    ap.add_argument("--repeats", type=int, default=0)
+    ap.add_argument("--confirm", type=int, default=8,
+                    help="re-measure this many of the best points (with --repeats; 0: off)")
+    ap.add_argument("--repeats", type=int, default=4)
     ap.add_argument("--batch-modes", default="persistent,launches",
                     help="batched256: which tables to tune (persistent, launches)")
     a = ap.parse_args()
