@@ -9,11 +9,12 @@ then measures energy only for the N fastest points; without it every point
 gets an energy window.  Results are cached (JSON lines) so a sweep resumes.
 
 --confirm C --repeats R (default 8 and 4; --confirm 0 turns it off)
-re-measures the C best points of the objective R more times, the C points one after the other in each round (so that slow
-drifts of power or temperature reach all of them alike), and keeps the point
-with the best median: near-ties among the top points (GB300, 4096^2 / 17 x
-17: the three most energy-efficient within 0.14 %, below one window's
-spread) are then decided on several windows instead of one.
+re-measures the C best points of the objective R more times, the C points
+one after the other in each round (so that slow drifts of power or
+temperature reach all of them alike), and keeps the point with the best
+median: near-ties among the top points (GB300, 4096^2 / 17 x 17: the three
+most energy-efficient within 0.14 %, below one window's spread) are then
+decided on several windows instead of one.
 """
 from __future__ import annotations
 
